@@ -1,0 +1,185 @@
+"""Two further formulations of the projection, for tiny inputs only.
+
+TEST INFRASTRUCTURE ONLY. Written independently of lt_oracle.c (own lattice
+walk, own unwrapping, own camera rays, connectivity read from the table
+printed in the paper, tests/golden/connectivity.txt), so that agreement with
+the oracle pins its arithmetic:
+
+  * `render_barycentric`: every (pixel, tetrahedron) pair; the chord is the
+    length of the parameter interval on which all four barycentric
+    coordinates of the ray point are >= 0 (the definition of "inside").
+  * `render_cell_projection`: the front/back face form of Eq. 13 (Sec. 4.4):
+    every face hit by the ray adds rho * |X - c| to a back-face sum or to a
+    front-face sum, c the camera location; the pixel is back minus front.
+
+Both draw every periodic copy of every tetrahedron for periodic orthographic
+windows by brute force over image-period shifts in [-2, 2].
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+_TABLE = None
+
+
+def connectivity() -> np.ndarray:
+    global _TABLE
+    if _TABLE is None:
+        path = os.path.join(os.path.dirname(__file__), "..", "tests", "golden", "connectivity.txt")
+        rows = [list(map(int, ln.split())) for ln in open(path) if ln.strip() and not ln.startswith("#")]
+        _TABLE = np.array(rows, dtype=np.int64)
+    return _TABLE
+
+
+def lattice_tets(pos, N: int, box: float = 1.0, total_mass: float = 1.0):
+    """All tetrahedra of the periodic lattice: vertices [6N^3][4][3] and
+    densities [6N^3], tetrahedron id = 6 * (i + N (j + N k)) + s."""
+    p = np.asarray(pos, dtype=np.float64).reshape(N ** 3, -1)[:, :3]
+    h = box / N
+    tab = connectivity()
+    verts = np.zeros((6 * N ** 3, 4, 3))
+    t = 0
+    for k in range(N):
+        for j in range(N):
+            for i in range(N):
+                for s in range(6):
+                    for c in range(4):
+                        n = int(tab[s, c])
+                        ii, jj, kk = i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1)
+                        pid = (ii % N) + N * ((jj % N) + N * (kk % N))
+                        q = np.array([ii, jj, kk], dtype=np.float64) * h
+                        d = p[pid] - q
+                        d = d - box * np.round(d / box)
+                        verts[t, c] = q + d
+                    t += 1
+    a = verts[:, 1] - verts[:, 0]
+    b = verts[:, 2] - verts[:, 0]
+    c = verts[:, 3] - verts[:, 0]
+    vol = np.einsum("ij,ij->i", a, np.cross(b, c)) / 6.0
+    m = total_mass / (6.0 * N ** 3)
+    with np.errstate(divide="ignore"):
+        rho = np.where(vol != 0, m / np.abs(vol), 0.0)
+    return verts, rho, vol
+
+
+def _frame(cam):
+    f = np.asarray(cam["fwd"], dtype=np.float64)
+    f = f / np.linalg.norm(f)
+    r = np.cross(np.asarray(cam["up"], dtype=np.float64), f)
+    r = r / np.linalg.norm(r)
+    u = np.cross(f, r)
+    return r, u, f
+
+
+def pixel_rays(cam):
+    """Origins and unit directions [H*W][3] of all pixel-centre rays."""
+    W, H = cam["W"], cam["H"]
+    r, u, f = _frame(cam)
+    px, py = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    px, py = px.ravel(), py.ravel()
+    if cam["type"] == "ortho":
+        lo, hi = cam["lo"], cam["hi"]
+        a = lo[0] + px * (hi[0] - lo[0]) / W
+        b = lo[1] + py * (hi[1] - lo[1]) / H
+        o = a[:, None] * r + b[:, None] * u
+        d = np.broadcast_to(f, o.shape).copy()
+        return o, d, False
+    ty = math.tan(math.radians(cam["fov_y_deg"]) / 2)
+    tx = ty * W / H
+    xt = tx * (2 * px / W - 1)
+    yt = ty * (2 * py / H - 1)
+    d = f + xt[:, None] * r + yt[:, None] * u
+    d = d / np.linalg.norm(d, axis=1, keepdims=True)
+    o = np.broadcast_to(np.asarray(cam["eye"], dtype=np.float64), d.shape).copy()
+    return o, d, True
+
+
+def _copies(cam):
+    if cam["type"] == "ortho" and cam.get("wrap", False):
+        r, u, _ = _frame(cam)
+        pu = (cam["hi"][0] - cam["lo"][0]) * r
+        pv = (cam["hi"][1] - cam["lo"][1]) * u
+        return [sx * pu + sy * pv for sx in range(-2, 3) for sy in range(-2, 3)]
+    return [np.zeros(3)]
+
+
+def _chord_barycentric(v, o, d, halfline):
+    M = np.vstack([v.T, np.ones(4)])  # columns are [v_i; 1]
+    Minv = np.linalg.inv(M)
+    lam0 = (Minv[:, :3] @ o.T) + Minv[:, 3:4]  # [4][P]
+    mu = Minv[:, :3] @ d.T
+    P = o.shape[0]
+    lo = np.full(P, -np.inf if not halfline else 0.0)
+    hi = np.full(P, np.inf)
+    ok = np.ones(P, dtype=bool)
+    for i in range(4):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            s = -lam0[i] / mu[i]
+        pos = mu[i] > 0
+        neg = mu[i] < 0
+        zer = mu[i] == 0
+        lo = np.where(pos, np.maximum(lo, s), lo)
+        hi = np.where(neg, np.minimum(hi, s), hi)
+        ok &= ~(zer & (lam0[i] < 0))
+    return np.where(ok & (hi > lo), hi - lo, 0.0)
+
+
+def render_barycentric(pos, N: int, cam: dict, box: float = 1.0, total_mass: float = 1.0) -> np.ndarray:
+    verts, rho, vol = lattice_tets(pos, N, box, total_mass)
+    o, d, half = pixel_rays(cam)
+    img = np.zeros(o.shape[0])
+    for shift in _copies(cam):
+        for t in range(len(rho)):
+            if vol[t] == 0:
+                continue
+            img += rho[t] * _chord_barycentric(verts[t] + shift, o, d, half)
+    return img.reshape(cam["H"], cam["W"])
+
+
+def _face_hits(a, b, c, o, d):
+    """Ray / triangle intersection (all rays against one triangle):
+    parameter s and a hit mask (barycentric coordinates all >= 0)."""
+    e1, e2 = b - a, c - a
+    pvec = np.cross(d, e2)
+    det = pvec @ e1
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = 1.0 / det
+        tvec = o - a
+        uu = np.einsum("ij,ij->i", tvec, pvec) * inv
+        qvec = np.cross(tvec, e1)
+        vv = np.einsum("ij,ij->i", qvec, d) * inv
+        s = (qvec @ e2) * inv
+    hit = (det != 0) & (uu >= 0) & (vv >= 0) & (uu + vv <= 1)
+    return s, hit
+
+
+def render_cell_projection(pos, N: int, cam: dict, box: float = 1.0, total_mass: float = 1.0,
+                           far: float = 100.0) -> np.ndarray:
+    verts, rho, vol = lattice_tets(pos, N, box, total_mass)
+    o, d, half = pixel_rays(cam)
+    # camera location c: the eye, or a point far behind the orthographic image plane
+    c = o if half else o - far * d
+    front = np.zeros(o.shape[0])
+    back = np.zeros(o.shape[0])
+    for shift in _copies(cam):
+        for t in range(len(rho)):
+            if vol[t] == 0:
+                continue
+            v = verts[t] + shift
+            for i in range(4):
+                a, b, cc = v[(i + 1) % 4], v[(i + 2) % 4], v[(i + 3) % 4]
+                n = np.cross(b - a, cc - a)
+                if n @ (v[i] - a) > 0:
+                    n = -n  # outward normal
+                s, hit = _face_hits(a, b, cc, o, d)
+                if half:
+                    hit &= s >= 0
+                X = o + s[:, None] * d
+                dist = np.linalg.norm(X - c, axis=1)
+                facing = d @ n
+                front += np.where(hit & (facing < 0), rho[t] * dist, 0.0)
+                back += np.where(hit & (facing > 0), rho[t] * dist, 0.0)
+    return (back - front).reshape(cam["H"], cam["W"])

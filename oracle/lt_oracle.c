@@ -1,0 +1,509 @@
+/*
+ * FP64 CPU oracle for the line-of-sight projection of the Lagrangian
+ * tetrahedral tessellation (Kaehler, Hahn & Abel, arXiv:1208.3206).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, plain definition that the
+ * GPU path is checked against. Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load it; the product library never does.
+ * It shares no code, header, table or constant with the CUDA sources.
+ *
+ * What it computes, step by step in the paper's order:
+ *   - the particle id <-> lattice index map, Eq. 8 (Sec. 4.1);
+ *   - the six tetrahedra of each lattice cube from the connectivity table of
+ *     Sec. 4.1 / Fig. "TetraSplit" (Sec. 3.1);
+ *   - the signed volume, Eq. 9, and the per-tetrahedron density m / |V|,
+ *     Eq. 3 (Sec. 3.2);
+ *   - the line-of-sight projection q_proj = sum_i q_i * dl_i, Eq. 6
+ *     (Sec. 3.2), with dl_i the exact length of the pixel ray inside
+ *     tetrahedron i, found by clipping the ray against the four face planes.
+ *   - the gradient of that projection with respect to particle positions,
+ *     by differentiating rho_i * dl_i directly (density through the volume,
+ *     chord through the entry and exit face planes).
+ *
+ * Readings where the paper is silent (each is listed in the design doc):
+ *   - corner n of a cube is lattice point (i+(n&1), j+((n>>1)&1), k+((n>>2)&1));
+ *   - the lattice is periodic: N^3 cubes, corner indices taken mod N, each
+ *     vertex unwrapped to the minimum image of its Lagrangian position;
+ *   - m = total_mass / (6 N^3) for every tetrahedron;
+ *   - a pixel's value is the projection along the ray through its centre;
+ *   - a tetrahedron with V == 0 exactly contributes nothing;
+ *   - orthographic windows may be periodic in both image axes (wrap), in
+ *     which case every periodic copy of a tetrahedron is drawn; perspective
+ *     views draw the single unwrapped copy of the lattice.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Connectivity of the six tetrahedra inside one cube (Sec. 4.1). */
+static const int CUBE_TETS[6][4] = {
+    {1, 0, 2, 4}, {3, 1, 2, 4}, {3, 5, 1, 4}, {3, 6, 5, 4}, {3, 2, 6, 4}, {3, 7, 5, 6}};
+
+typedef struct {
+  int type;           /* 0 orthographic, 1 perspective */
+  double eye[3];      /* perspective eye position */
+  double fwd[3];      /* viewing direction (need not be unit) */
+  double up[3];       /* up hint (need not be unit or orthogonal) */
+  double fov_y_deg;   /* perspective vertical field of view */
+  double lo[2], hi[2];/* orthographic window in (right, up) coordinates */
+  int W, H;           /* image size in pixels */
+  int wrap;           /* orthographic only: window is periodic */
+} orc_camera;
+
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_BEHIND_EYE = 2 };
+
+/* ---------- small vector helpers ---------- */
+static void sub3(const double* a, const double* b, double* o) {
+  o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2];
+}
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double* a, const double* b, double* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+static void normalize3(double* a) {
+  double n = sqrt(dot3(a, a));
+  a[0] /= n; a[1] /= n; a[2] /= n;
+}
+
+/* ---------- camera frame ---------- */
+typedef struct {
+  int persp, W, H, wrap;
+  double eye[3], r[3], u[3], f[3];
+  double tan_x, tan_y;
+  double lo[2], hi[2];
+} frame_t;
+
+static int frame_init(const orc_camera* c, frame_t* fr) {
+  if (c->W <= 0 || c->H <= 0) return ORC_ERR_ARG;
+  fr->persp = c->type == 1;
+  fr->W = c->W; fr->H = c->H;
+  fr->wrap = (!fr->persp) && c->wrap;
+  memcpy(fr->eye, c->eye, sizeof fr->eye);
+  memcpy(fr->f, c->fwd, sizeof fr->f);
+  normalize3(fr->f);
+  cross3(c->up, fr->f, fr->r); /* right = up x forward */
+  normalize3(fr->r);
+  cross3(fr->f, fr->r, fr->u); /* true up = forward x right */
+  fr->tan_y = tan(0.5 * c->fov_y_deg * M_PI / 180.0);
+  fr->tan_x = fr->tan_y * (double)c->W / (double)c->H;
+  fr->lo[0] = c->lo[0]; fr->lo[1] = c->lo[1];
+  fr->hi[0] = c->hi[0]; fr->hi[1] = c->hi[1];
+  return ORC_OK;
+}
+
+/* Continuous pixel coordinate of a world point: pixel px has its centre at
+ * fx == px. Returns 0 if the point is not in front of a perspective eye. */
+static int to_pixel(const frame_t* fr, const double* X, double* fx, double* fy) {
+  if (!fr->persp) {
+    double a = dot3(fr->r, X), b = dot3(fr->u, X);
+    *fx = (a - fr->lo[0]) / (fr->hi[0] - fr->lo[0]) * fr->W - 0.5;
+    *fy = (b - fr->lo[1]) / (fr->hi[1] - fr->lo[1]) * fr->H - 0.5;
+    return 1;
+  }
+  double c[3];
+  sub3(X, fr->eye, c);
+  double z = dot3(fr->f, c);
+  if (!(z > 0.0)) return 0;
+  double xt = dot3(fr->r, c) / z, yt = dot3(fr->u, c) / z;
+  *fx = (xt / fr->tan_x + 1.0) * 0.5 * fr->W - 0.5;
+  *fy = (yt / fr->tan_y + 1.0) * 0.5 * fr->H - 0.5;
+  return 1;
+}
+
+/* Ray through the centre of (unwrapped) pixel (px, py): origin o, unit
+ * direction d. Orthographic rays are full lines, perspective rays start at
+ * the eye. */
+static void pixel_ray(const frame_t* fr, long px, long py, double* o, double* d) {
+  if (!fr->persp) {
+    double a = fr->lo[0] + (px + 0.5) * (fr->hi[0] - fr->lo[0]) / fr->W;
+    double b = fr->lo[1] + (py + 0.5) * (fr->hi[1] - fr->lo[1]) / fr->H;
+    for (int q = 0; q < 3; ++q) { o[q] = a * fr->r[q] + b * fr->u[q]; d[q] = fr->f[q]; }
+    return;
+  }
+  double xt = fr->tan_x * (2.0 * (px + 0.5) / fr->W - 1.0);
+  double yt = fr->tan_y * (2.0 * (py + 0.5) / fr->H - 1.0);
+  for (int q = 0; q < 3; ++q) { o[q] = fr->eye[q]; d[q] = fr->f[q] + xt * fr->r[q] + yt * fr->u[q]; }
+  normalize3(d);
+}
+
+/* ---------- tessellation ---------- */
+
+/* Unwrapped corner position: Lagrangian point of lattice index (ii,jj,kk)
+ * (not reduced mod N) plus the minimum-image displacement of the particle
+ * stored at that index mod N. Particle id follows Eq. 8 with d0 = d1 = N. */
+static void corner_position(const double* pos, int N, double box, long ii, long jj, long kk, double* v) {
+  long i = ii % N, j = jj % N, k = kk % N;
+  long id = i + (long)N * (j + (long)N * k);
+  double h = box / N;
+  double q[3] = {ii * h, jj * h, kk * h};
+  for (int a = 0; a < 3; ++a) {
+    double dd = pos[3 * id + a] - q[a];
+    dd -= box * nearbyint(dd / box);
+    v[a] = q[a] + dd;
+  }
+}
+
+/* Vertices of tetrahedron s of cube (i,j,k), in the table's order. */
+static void tet_vertices(const double* pos, int N, double box, long i, long j, long k, int s, double v[4][3]) {
+  for (int c = 0; c < 4; ++c) {
+    int n = CUBE_TETS[s][c];
+    corner_position(pos, N, box, i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1), v[c]);
+  }
+}
+
+/* Signed volume, Eq. 9. */
+static double tet_volume(double v[4][3]) {
+  double a[3], b[3], c[3], bc[3];
+  sub3(v[1], v[0], a); sub3(v[2], v[0], b); sub3(v[3], v[0], c);
+  cross3(b, c, bc);
+  return dot3(a, bc) / 6.0;
+}
+
+/* Exact chord of the ray o + s d (|d| = 1) through the tetrahedron: clip
+ * against the four face planes. s starts at -inf for a full line and at 0
+ * for a half-line. Optionally reports which face bounds the entry / exit. */
+static double ray_chord(double v[4][3], const double* o, const double* d, int halfline, int* f_in,
+                        int* f_out, double* s_in_out, double* s_out_out) {
+  double s_in = halfline ? 0.0 : -INFINITY, s_out = INFINITY;
+  int fin = -1, fout = -1;
+  for (int i = 0; i < 4; ++i) {
+    const double *a = v[(i + 1) & 3], *b = v[(i + 2) & 3], *c = v[(i + 3) & 3];
+    double e1[3], e2[3], n[3], t[3];
+    sub3(b, a, e1); sub3(c, a, e2);
+    cross3(e1, e2, n);
+    sub3(v[i], a, t);
+    if (dot3(n, t) > 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; } /* outward */
+    double ao[3];
+    sub3(a, o, ao);
+    double den = dot3(n, d), num = dot3(n, ao); /* inside: s * den <= num */
+    if (den > 0.0) {
+      double s = num / den;
+      if (s < s_out) { s_out = s; fout = i; }
+    } else if (den < 0.0) {
+      double s = num / den;
+      if (s > s_in) { s_in = s; fin = i; }
+    } else if (num < 0.0) {
+      return 0.0;
+    }
+  }
+  if (f_in) *f_in = fin;
+  if (f_out) *f_out = fout;
+  if (s_in_out) *s_in_out = s_in;
+  if (s_out_out) *s_out_out = s_out;
+  return s_out > s_in ? s_out - s_in : 0.0;
+}
+
+/* Range of periodic image shifts (in units of W) that bring the pixel span
+ * [a, b] into overlap with [lo, hi]. */
+static void shift_range(long a, long b, long lo, long hi, long period, int wrap, long* s0, long* s1) {
+  if (!wrap) { *s0 = 0; *s1 = 0; return; }
+  /* need a + s*period <= hi and b + s*period >= lo */
+  double lo_s = ceil((double)(lo - b) / period), hi_s = floor((double)(hi - a) / period);
+  *s0 = (long)lo_s; *s1 = (long)hi_s;
+}
+
+/* Pixel bounding box of a tetrahedron: pixels whose centres lie inside the
+ * bounding box of the projected vertices. Returns 0 when the tetrahedron
+ * cannot be projected (a vertex at or behind the perspective eye). */
+static int tet_pixel_box(const frame_t* fr, double v[4][3], long* x0, long* x1, long* y0, long* y1) {
+  double mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+  for (int c = 0; c < 4; ++c) {
+    double fx, fy;
+    if (!to_pixel(fr, v[c], &fx, &fy)) return 0;
+    if (fx < mnx) mnx = fx;
+    if (fx > mxx) mxx = fx;
+    if (fy < mny) mny = fy;
+    if (fy > mxy) mxy = fy;
+  }
+  *x0 = (long)ceil(mnx); *x1 = (long)floor(mxx);
+  *y0 = (long)ceil(mny); *y1 = (long)floor(mxy);
+  return 1;
+}
+
+static int num_threads(int req) {
+#ifdef _OPENMP
+  return req > 0 ? req : omp_get_max_threads();
+#else
+  (void)req;
+  return 1;
+#endif
+}
+
+/*
+ * Column-density image(s). crops[4*c .. 4*c+3] = (x0, y0, w, h) of crop c in
+ * pixel coordinates of the W x H frame; out holds the crops one after the
+ * other, each row-major [h][w]. n_frag (optional) receives the number of
+ * (tetrahedron, pixel) pairs with a positive chord inside the crops, and
+ * n_degen (optional) the number of tetrahedra with V == 0.
+ */
+int orc_render(const double* pos, int N, double box, double total_mass, const orc_camera* cam,
+               const int* crops, int ncrops, double* out, long long* n_frag, long long* n_degen,
+               int nthreads) {
+  frame_t fr;
+  if (N <= 0 || box <= 0 || ncrops <= 0 || frame_init(cam, &fr) != ORC_OK) return ORC_ERR_ARG;
+  long total = 0;
+  long* coff = (long*)malloc(sizeof(long) * (ncrops + 1));
+  coff[0] = 0;
+  for (int c = 0; c < ncrops; ++c) coff[c + 1] = coff[c] + (long)crops[4 * c + 2] * crops[4 * c + 3];
+  total = coff[ncrops];
+  int T = num_threads(nthreads);
+  double* bufs = (double*)calloc((size_t)T * total, sizeof(double));
+  long long* frags = (long long*)calloc(T, sizeof(long long));
+  long long* degen = (long long*)calloc(T, sizeof(long long));
+  int* errs = (int*)calloc(T, sizeof(int));
+  const double m = total_mass / (6.0 * (double)N * N * N);
+  const long ncubes = (long)N * N * N;
+
+#pragma omp parallel num_threads(T)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double* img = bufs + (size_t)tid * total;
+#pragma omp for schedule(static)
+    for (long cube = 0; cube < ncubes; ++cube) {
+      long i = cube % N, j = (cube / N) % N, k = cube / ((long)N * N);
+      for (int s = 0; s < 6; ++s) {
+        double v[4][3];
+        tet_vertices(pos, N, box, i, j, k, s, v);
+        double V = tet_volume(v);
+        if (V == 0.0) { degen[tid]++; continue; }
+        double rho = m / fabs(V); /* Eq. 3 */
+        long bx0, bx1, by0, by1;
+        if (!tet_pixel_box(&fr, v, &bx0, &bx1, &by0, &by1)) { errs[tid] = ORC_ERR_BEHIND_EYE; continue; }
+        if (bx0 > bx1 || by0 > by1) continue;
+        for (int c = 0; c < ncrops; ++c) {
+          long cx0 = crops[4 * c], cy0 = crops[4 * c + 1];
+          long cx1 = cx0 + crops[4 * c + 2] - 1, cy1 = cy0 + crops[4 * c + 3] - 1;
+          long sx0, sx1, sy0, sy1;
+          shift_range(bx0, bx1, cx0, cx1, fr.W, fr.wrap, &sx0, &sx1);
+          shift_range(by0, by1, cy0, cy1, fr.H, fr.wrap, &sy0, &sy1);
+          for (long sy = sy0; sy <= sy1; ++sy)
+            for (long sx = sx0; sx <= sx1; ++sx) {
+              /* pixel (px + sx W, py + sy H) of the frame sees this copy through
+               * the unwrapped pixel (px, py) */
+              long px0 = bx0 > cx0 - sx * fr.W ? bx0 : cx0 - sx * fr.W;
+              long px1 = bx1 < cx1 - sx * fr.W ? bx1 : cx1 - sx * fr.W;
+              long py0 = by0 > cy0 - sy * fr.H ? by0 : cy0 - sy * fr.H;
+              long py1 = by1 < cy1 - sy * fr.H ? by1 : cy1 - sy * fr.H;
+              for (long py = py0; py <= py1; ++py)
+                for (long px = px0; px <= px1; ++px) {
+                  double o[3], d[3];
+                  pixel_ray(&fr, px, py, o, d);
+                  double dl = ray_chord(v, o, d, fr.persp, NULL, NULL, NULL, NULL);
+                  if (dl > 0.0) {
+                    long X = px + sx * fr.W - cx0, Y = py + sy * fr.H - cy0;
+                    img[coff[c] + Y * crops[4 * c + 2] + X] += rho * dl; /* Eq. 6 */
+                    frags[tid]++;
+                  }
+                }
+            }
+        }
+      }
+    }
+  }
+  /* fixed-order reduction of the per-thread images */
+  memset(out, 0, sizeof(double) * total);
+  long long nf = 0, nd = 0;
+  int err = ORC_OK;
+  for (int t = 0; t < T; ++t) {
+    const double* img = bufs + (size_t)t * total;
+    for (long p = 0; p < total; ++p) out[p] += img[p];
+    nf += frags[t];
+    nd += degen[t];
+    if (errs[t]) err = errs[t];
+  }
+  if (n_frag) *n_frag = nf;
+  if (n_degen) *n_degen = nd;
+  free(bufs); free(frags); free(degen); free(errs); free(coff);
+  return err;
+}
+
+/* Per-tetrahedron signed volume (Eq. 9) and density (Eq. 3), tetrahedron
+ * id = 6 * cube + s with cube = i + N (j + N k). rho = 0 when V == 0. */
+int orc_tets(const double* pos, int N, double box, double total_mass, double* vol, double* rho) {
+  if (N <= 0 || box <= 0) return ORC_ERR_ARG;
+  const double m = total_mass / (6.0 * (double)N * N * N);
+  const long ncubes = (long)N * N * N;
+#pragma omp parallel for schedule(static)
+  for (long cube = 0; cube < ncubes; ++cube) {
+    long i = cube % N, j = (cube / N) % N, k = cube / ((long)N * N);
+    for (int s = 0; s < 6; ++s) {
+      double v[4][3];
+      tet_vertices(pos, N, box, i, j, k, s, v);
+      double V = tet_volume(v);
+      vol[6 * cube + s] = V;
+      rho[6 * cube + s] = V == 0.0 ? 0.0 : m / fabs(V);
+    }
+  }
+  return ORC_OK;
+}
+
+/* d s / d a for the crossing s of the ray with the plane of face (a, b, c)
+ * when vertex a moves: the plane moves by lambda_a(X) * delta at the crossing
+ * point X, so ds = lambda_a(X) (n . delta) / (n . d). Adds scale * that to g. */
+static void add_crossing_grad(const double* a, const double* b, const double* c, const double* X,
+                              const double* d, double scale, double* g) {
+  double e1[3], e2[3], n[3], bx[3], cx[3], t[3];
+  sub3(b, a, e1); sub3(c, a, e2);
+  cross3(e1, e2, n);
+  sub3(b, X, bx); sub3(c, X, cx);
+  cross3(bx, cx, t);
+  double lam = dot3(t, n) / dot3(n, n);
+  double den = dot3(n, d);
+  for (int q = 0; q < 3; ++q) g[q] += scale * lam * n[q] / den;
+}
+
+/*
+ * Gradient of L with respect to particle positions, given dL/dI for every
+ * pixel of the full W x H frame (row-major). For each (tetrahedron, pixel)
+ * pair with a positive chord: d(rho dl) = dl d rho + rho d dl, with
+ * d rho / d v = -(rho / V) dV/dv (Eq. 3 and 9) and dl = s_out - s_in moving
+ * with the exit and entry face planes.
+ */
+int orc_grad(const double* pos, int N, double box, double total_mass, const orc_camera* cam,
+             const double* dLdI, double* grad, int nthreads) {
+  frame_t fr;
+  if (N <= 0 || box <= 0 || frame_init(cam, &fr) != ORC_OK) return ORC_ERR_ARG;
+  const long np = (long)N * N * N;
+  int T = num_threads(nthreads);
+  double* bufs = (double*)calloc((size_t)T * np * 3, sizeof(double));
+  int* errs = (int*)calloc(T, sizeof(int));
+  const double m = total_mass / (6.0 * (double)N * N * N);
+#pragma omp parallel num_threads(T)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double* G = bufs + (size_t)tid * np * 3;
+#pragma omp for schedule(static)
+    for (long cube = 0; cube < np; ++cube) {
+      long i = cube % N, j = (cube / N) % N, k = cube / ((long)N * N);
+      for (int s = 0; s < 6; ++s) {
+        double v[4][3];
+        tet_vertices(pos, N, box, i, j, k, s, v);
+        double V = tet_volume(v);
+        if (V == 0.0) continue;
+        double rho = m / fabs(V);
+        /* dV/dv_c for the table order (Eq. 9) */
+        double a[3], b[3], c[3], dV[4][3];
+        sub3(v[1], v[0], a); sub3(v[2], v[0], b); sub3(v[3], v[0], c);
+        cross3(b, c, dV[1]); cross3(c, a, dV[2]); cross3(a, b, dV[3]);
+        for (int q = 0; q < 3; ++q) {
+          dV[1][q] /= 6.0; dV[2][q] /= 6.0; dV[3][q] /= 6.0;
+          dV[0][q] = -(dV[1][q] + dV[2][q] + dV[3][q]);
+        }
+        long ids[4];
+        for (int cc = 0; cc < 4; ++cc) {
+          int n = CUBE_TETS[s][cc];
+          long ii = (i + (n & 1)) % N, jj = (j + ((n >> 1) & 1)) % N, kk = (k + ((n >> 2) & 1)) % N;
+          ids[cc] = ii + (long)N * (jj + (long)N * kk);
+        }
+        long bx0, bx1, by0, by1;
+        if (!tet_pixel_box(&fr, v, &bx0, &bx1, &by0, &by1)) { errs[tid] = ORC_ERR_BEHIND_EYE; continue; }
+        if (bx0 > bx1 || by0 > by1) continue;
+        long sx0, sx1, sy0, sy1;
+        shift_range(bx0, bx1, 0, fr.W - 1, fr.W, fr.wrap, &sx0, &sx1);
+        shift_range(by0, by1, 0, fr.H - 1, fr.H, fr.wrap, &sy0, &sy1);
+        for (long sy = sy0; sy <= sy1; ++sy)
+          for (long sx = sx0; sx <= sx1; ++sx) {
+            long px0 = bx0 > -sx * fr.W ? bx0 : -sx * fr.W;
+            long px1 = bx1 < fr.W - 1 - sx * fr.W ? bx1 : fr.W - 1 - sx * fr.W;
+            long py0 = by0 > -sy * fr.H ? by0 : -sy * fr.H;
+            long py1 = by1 < fr.H - 1 - sy * fr.H ? by1 : fr.H - 1 - sy * fr.H;
+            for (long py = py0; py <= py1; ++py)
+              for (long px = px0; px <= px1; ++px) {
+                double o[3], d[3], s_in, s_out;
+                int fin, fout;
+                pixel_ray(&fr, px, py, o, d);
+                double dl = ray_chord(v, o, d, fr.persp, &fin, &fout, &s_in, &s_out);
+                if (!(dl > 0.0)) continue;
+                double g = dLdI[(py + sy * fr.H) * (long)fr.W + (px + sx * fr.W)];
+                if (g == 0.0) continue;
+                double gv[4][3];
+                memset(gv, 0, sizeof gv);
+                for (int cc = 0; cc < 4; ++cc)
+                  for (int q = 0; q < 3; ++q) gv[cc][q] = -dl * rho / V * dV[cc][q];
+                /* chord through the exit (+) and entry (-) face planes */
+                for (int side = 0; side < 2; ++side) {
+                  int f = side == 0 ? fout : fin;
+                  if (f < 0) continue; /* half-line start at the eye does not move */
+                  double sgn = side == 0 ? rho : -rho;
+                  double sv = side == 0 ? s_out : s_in;
+                  double X[3] = {o[0] + sv * d[0], o[1] + sv * d[1], o[2] + sv * d[2]};
+                  int fa = (f + 1) & 3, fb = (f + 2) & 3, fc = (f + 3) & 3;
+                  add_crossing_grad(v[fa], v[fb], v[fc], X, d, sgn, gv[fa]);
+                  add_crossing_grad(v[fb], v[fc], v[fa], X, d, sgn, gv[fb]);
+                  add_crossing_grad(v[fc], v[fa], v[fb], X, d, sgn, gv[fc]);
+                }
+                for (int cc = 0; cc < 4; ++cc)
+                  for (int q = 0; q < 3; ++q) G[3 * ids[cc] + q] += g * gv[cc][q];
+              }
+          }
+      }
+    }
+  }
+  memset(grad, 0, sizeof(double) * np * 3);
+  int err = ORC_OK;
+  for (int t = 0; t < T; ++t) {
+    const double* G = bufs + (size_t)t * np * 3;
+    for (long p = 0; p < np * 3; ++p) grad[p] += G[p];
+    if (errs[t]) err = errs[t];
+  }
+  free(bufs); free(errs);
+  return err;
+}
+
+/* ---------- entry points used by the oracle's own pins ---------- */
+
+/* Chord of one ray through one tetrahedron (v: 4 x 3 doubles). */
+double orc_chord(const double* v12, const double* o, const double* d, int halfline) {
+  double v[4][3];
+  memcpy(v, v12, sizeof v);
+  double dn[3] = {d[0], d[1], d[2]};
+  normalize3(dn);
+  return ray_chord(v, o, dn, halfline, NULL, NULL, NULL, NULL);
+}
+
+/* Vertices (4 x 3) of tetrahedron s of cube (i, j, k) after unwrapping. */
+int orc_tet_vertices(const double* pos, int N, double box, int i, int j, int k, int s, double* out12) {
+  if (N <= 0 || s < 0 || s > 5) return ORC_ERR_ARG;
+  double v[4][3];
+  tet_vertices(pos, N, box, i, j, k, s, v);
+  memcpy(out12, v, sizeof v);
+  return ORC_OK;
+}
+
+/* Projection (Eq. 6) of an arbitrary set of tetrahedra with given constant
+ * densities, full W x H frame, same pixel and ray conventions as orc_render
+ * (no periodic copies). */
+int orc_render_soup(const double* verts /* [n][4][3] */, const double* dens, long n, const orc_camera* cam,
+                    double* out) {
+  frame_t fr;
+  if (frame_init(cam, &fr) != ORC_OK) return ORC_ERR_ARG;
+  memset(out, 0, sizeof(double) * fr.W * fr.H);
+  for (long t = 0; t < n; ++t) {
+    double v[4][3];
+    memcpy(v, verts + 12 * t, sizeof v);
+    long x0, x1, y0, y1;
+    if (!tet_pixel_box(&fr, v, &x0, &x1, &y0, &y1)) return ORC_ERR_BEHIND_EYE;
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x1 > fr.W - 1) x1 = fr.W - 1;
+    if (y1 > fr.H - 1) y1 = fr.H - 1;
+    for (long py = y0; py <= y1; ++py)
+      for (long px = x0; px <= x1; ++px) {
+        double o[3], d[3];
+        pixel_ray(&fr, px, py, o, d);
+        out[py * fr.W + px] += dens[t] * ray_chord(v, o, d, fr.persp, NULL, NULL, NULL, NULL);
+      }
+  }
+  return ORC_OK;
+}

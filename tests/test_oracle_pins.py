@@ -1,0 +1,324 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by geometry.
+
+Each test checks the oracle against something other than itself: the
+connectivity table printed in the paper (tests/golden/connectivity.txt),
+closed forms, invariants of the tessellation, or two independent brute-force
+formulations. A plausible mistake in the oracle (a wrong corner numbering, a
+dropped periodic copy, a sign error in an orientation, a wrong ray) breaks at
+least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import bruteforce as bf
+from lt_inputs import ZeldovichField, camera_dict, ortho_z
+
+
+def lattice_positions(N, box=1.0, disp=None, dtype=np.float32):
+    idx = np.arange(N ** 3)
+    q = np.stack([idx % N, (idx // N) % N, idx // (N * N)], axis=1) * (box / N)
+    x = q if disp is None else q + disp(q)
+    x = np.mod(x, box)
+    out = np.zeros((N ** 3, 4), dtype=dtype)
+    out[:, :3] = x
+    out[:, :3] = np.where(out[:, :3] >= dtype(box), dtype(0), out[:, :3])
+    return out
+
+
+def offset_window(W, H, box=1.0, off=(0.0123, 0.0457)):
+    # a periodic window whose pixel centres avoid the lattice planes
+    return camera_dict("ortho", W, H, fwd=(0, 0, 1), up=(0, 1, 0), lo=off,
+                       hi=(off[0] + box, off[1] + box), wrap=True)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4.1 connectivity table (golden) and Eq. 9
+
+
+def test_connectivity_table_tiles_the_cube():
+    """The printed table with corner n -> (n&1, n>>1&1, n>>2&1) splits the
+    unit cube into six tetrahedra of volume -1/6 that cover it exactly once."""
+    tab = bf.connectivity()
+    corners = np.array([[(n & 1), (n >> 1) & 1, (n >> 2) & 1] for n in range(8)], dtype=np.float64)
+    rng = np.random.default_rng(0)
+    pts = rng.random((20000, 3))
+    inside = np.zeros(len(pts), dtype=int)
+    for row in tab:
+        v = corners[row]
+        vol = np.dot(v[1] - v[0], np.cross(v[2] - v[0], v[3] - v[0])) / 6.0
+        assert vol == pytest.approx(-1.0 / 6.0, abs=1e-15)
+        M = np.vstack([v.T, np.ones(4)])
+        lam = np.linalg.solve(M, np.vstack([pts.T, np.ones(len(pts))]))
+        inside += np.all(lam >= 0, axis=0)
+    assert np.all(inside == 1)
+
+
+def test_oracle_tets_follow_golden_table():
+    N, box = 3, 1.0
+    pos = lattice_positions(N, box)
+    tab = bf.connectivity()
+    h = box / N
+    for (i, j, k) in [(0, 0, 0), (2, 1, 0), (2, 2, 2)]:
+        for s in range(6):
+            v = oracle.tet_vertices(pos, N, i, j, k, s, box)
+            want = [[(i + (n & 1)) * h, (j + ((n >> 1) & 1)) * h, (k + ((n >> 2) & 1)) * h] for n in tab[s]]
+            np.testing.assert_allclose(v, want, atol=1e-7)
+
+
+def test_signed_volumes_unperturbed_and_total():
+    """Unperturbed: every tet has V = -h^3/6 (all six negative with this
+    table). Deformed, periodic: the signed volumes still sum to -box^3."""
+    N = 6
+    vol, rho = oracle.tet_volumes(lattice_positions(N), N)
+    np.testing.assert_allclose(vol, -1.0 / (6 * N ** 3), rtol=1e-6)
+    np.testing.assert_allclose(rho, 1.0, rtol=1e-6)  # m / |V| with M = 1 in a unit box
+    f = ZeldovichField.generate(16, -2.0, 6.0, 3)
+    vol, rho = oracle.tet_volumes(f.positions(3.0), 16)
+    assert (vol > 0).any()  # shell crossing inverts some tetrahedra
+    assert vol.sum() == pytest.approx(-1.0, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Eq. 6: chords and single tetrahedra
+
+
+def test_corner_tet_chord_closed_form():
+    """Tet (0,0,0),(a,0,0),(0,a,0),(0,0,a): chord along z at (x, y) is
+    a - x - y inside the triangle, along x at (y, z) it is a - y - z."""
+    a = 0.7
+    v = [[0, 0, 0], [a, 0, 0], [0, a, 0], [0, 0, a]]
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        x, y = rng.uniform(-0.2, 0.9, 2)
+        want = max(0.0, a - x - y) if (x >= 0 and y >= 0) else 0.0
+        assert oracle.chord(v, [x, y, -3.0], [0, 0, 1]) == pytest.approx(want, abs=1e-14)
+        assert oracle.chord(v, [5.0, x, y], [-1, 0, 0]) == pytest.approx(
+            max(0.0, a - x - y) if (x >= 0 and y >= 0) else 0.0, abs=1e-14)
+    # a half-line that starts inside the tet only measures the part ahead
+    assert oracle.chord(v, [0.1, 0.1, 0.2], [0, 0, 1], halfline=True) == pytest.approx(a - 0.2 - 0.2, abs=1e-14)
+
+
+def test_corner_tet_image_closed_form():
+    a = 0.6
+    v = np.array([[[0, 0, 0], [a, 0, 0], [0, a, 0], [0, 0, a]]], dtype=np.float64)
+    cam = camera_dict("ortho", 37, 41, fwd=(0, 0, 1), up=(0, 1, 0), lo=(-0.11, -0.07), hi=(0.71, 0.69))
+    img = oracle.render_soup(v, [2.5], cam)
+    xs = -0.11 + (np.arange(37) + 0.5) * (0.82 / 37)
+    ys = -0.07 + (np.arange(41) + 0.5) * (0.76 / 41)
+    X, Y = np.meshgrid(xs, ys)
+    want = np.where((X >= 0) & (Y >= 0), 2.5 * np.maximum(0.0, a - X - Y), 0.0)
+    np.testing.assert_allclose(img, want, atol=1e-13)
+
+
+def test_single_tet_mass_converges():
+    """Sum of rho * chord * pixel area -> rho |V| = m as the pixels shrink,
+    with O(h^2) error (the chord is piecewise linear over the projection)."""
+    rng = np.random.default_rng(7)
+    v = rng.uniform(0.2, 0.8, (1, 4, 3))
+    vol = abs(np.dot(v[0, 1] - v[0, 0], np.cross(v[0, 2] - v[0, 0], v[0, 3] - v[0, 0]))) / 6
+    dens = 1.0 / vol  # unit mass
+    errs = []
+    for W in (50, 100, 200, 400):
+        cam = camera_dict("ortho", W, W, fwd=(0.3, -0.2, 1.0), up=(0, 1, 0), lo=(-1.0, -1.0), hi=(1.5, 1.5))
+        img = oracle.render_soup(v, [dens], cam)
+        errs.append(abs(oracle.frame_mass(img, cam) - 1.0))
+    assert errs[-1] < 1e-3
+    assert errs[-1] < errs[0] / 10
+
+
+# ---------------------------------------------------------------------------
+# Lattices with known projections
+
+
+def test_unperturbed_lattice_is_uniform_column_density():
+    N = 8
+    cam = offset_window(61, 53)
+    img, nf, nd = oracle.render(lattice_positions(N), N, cam, return_counts=True)
+    np.testing.assert_allclose(img, 1.0, rtol=1e-12)
+    assert nd == 0
+    assert nf == 4 * N * 61 * 53  # every z-ray crosses exactly 4 tets per cube
+    # scaling with box and mass: column density = M / box^2
+    box, M = 2.0, 3.0
+    cam = offset_window(29, 31, box=box, off=(0.031, 0.077))
+    img = oracle.render(lattice_positions(N, box), N, cam, box=box, total_mass=M)
+    np.testing.assert_allclose(img, M / box ** 2, rtol=1e-12)
+
+
+def test_translated_and_z_displaced_lattices_stay_uniform():
+    """A uniform translation, or any displacement along the line of sight
+    (even with shell crossing and inverted tetrahedra), leaves every column
+    of the periodic box with the same mass."""
+    N = 8
+    cam = offset_window(47, 43)
+    shift = lambda q: np.broadcast_to(np.array([0.31, 0.17, 0.4]), q.shape)
+    img = oracle.render(lattice_positions(N, disp=shift, dtype=np.float64), N, cam)
+    np.testing.assert_allclose(img, 1.0, rtol=1e-11)
+
+    def dz(q):
+        d = np.zeros_like(q)
+        d[:, 2] = 0.25 * np.sin(2 * np.pi * q[:, 2]) + 0.1 * np.cos(2 * np.pi * q[:, 0]) * np.sin(2 * np.pi * q[:, 1])
+        return d
+
+    pos = lattice_positions(N, disp=dz)
+    vol, _ = oracle.tet_volumes(pos, N)
+    assert (vol > 0).any()
+    img = oracle.render(pos, N, cam)
+    np.testing.assert_allclose(img, 1.0, rtol=1e-10)
+
+
+def _pancake(N, A):
+    return lambda q: np.stack([-(A / (2 * np.pi)) * np.sin(2 * np.pi * q[:, 0]),
+                               np.zeros(len(q)), np.zeros(len(q))], axis=1)
+
+
+def test_pancake_closed_form_multistream():
+    """1D Zel'dovich pancake x = q - A/(2 pi) sin(2 pi q): each lattice cube
+    maps affinely onto [x_i, x_{i+1}], so the projection along z is exactly
+    sum over cube columns containing x of 1 / (N |x_{i+1} - x_i|); A > 1 gives
+    three streams and inverted tetrahedra."""
+    N, A = 16, 2.5
+    pos = lattice_positions(N, disp=_pancake(N, A))
+    W, H = 200, 24
+    cam = offset_window(W, H, off=(0.0031, 0.0123))
+    img = oracle.render(pos, N, cam)
+    # unwrapped column edges from the stored float32 positions
+    h = 1.0 / N
+    xs = []
+    for i in range(N + 1):
+        d = float(pos[i % N, 0]) - i * h
+        d -= round(d)
+        xs.append(i * h + d)
+    px = 0.0031 + (np.arange(W) + 0.5) / W
+    want = np.zeros(W)
+    for i in range(N):
+        a, b = sorted((xs[i], xs[i + 1]))
+        for s in (-1, 0, 1):
+            inside = (px >= a + s) & (px <= b + s)
+            want += np.where(inside, 1.0 / (N * (b - a)), 0.0)
+    assert want.max() > 3  # caustics
+    streams = np.zeros(W, dtype=int)
+    for i in range(N):
+        a, b = sorted((xs[i], xs[i + 1]))
+        for s in (-1, 0, 1):
+            streams += (px >= a + s) & (px <= b + s)
+    assert streams.max() == 3
+    np.testing.assert_allclose(img, np.broadcast_to(want, (H, W)), rtol=1e-9)
+
+
+def test_periodic_frame_mass_is_total_mass():
+    f = ZeldovichField.generate(16, -2.0, 6.0, 11)
+    pos = f.positions(1.5)
+    errs = []
+    for W in (128, 512):
+        img = oracle.render(pos, 16, ortho_z(W, W))
+        errs.append(abs(oracle.frame_mass(img, ortho_z(W, W)) - 1.0))
+    assert errs[1] < 1e-3 and errs[1] < errs[0]
+
+
+def test_perspective_unperturbed_lattice_is_box_chord():
+    """Unperturbed lattice of mean density 1 seen from outside: each pixel is
+    the length of its ray inside the unit box (slab intersection)."""
+    N = 6
+    pos = lattice_positions(N, dtype=np.float64)
+    eye = np.array([2.3, 1.7, 2.9])
+    cam = camera_dict("persp", 40, 36, eye=eye, fwd=np.array([0.5, 0.5, 0.5]) - eye, up=(0, 0, 1),
+                      fov_y_deg=50.0)
+    img = oracle.render(pos, N, cam)
+    o, d, _ = bf.pixel_rays(cam)
+    with np.errstate(divide="ignore"):
+        t1 = (0.0 - o) / d
+        t2 = (1.0 - o) / d
+    tmin = np.minimum(t1, t2).max(axis=1)
+    tmax = np.maximum(t1, t2).min(axis=1)
+    want = np.maximum(0.0, tmax - np.maximum(tmin, 0.0)).reshape(36, 40)
+    assert want.max() > 1.0
+    np.testing.assert_allclose(img, want, atol=1e-12)
+
+
+@pytest.mark.parametrize("view", ["ortho", "persp"])
+def test_oracle_matches_bruteforce_formulations(view):
+    N = 4
+    f = ZeldovichField.generate(N, -2.0, 2.0, 7)
+    pos = f.positions(1.8)
+    if view == "ortho":
+        cam = camera_dict("ortho", 24, 20, fwd=(0.2, 0.1, 1.0), up=(0, 1, 0), lo=(0.013, 0.021),
+                          hi=(1.013, 1.021), wrap=False)
+    else:
+        eye = np.array([0.5, -1.6, 1.3])
+        cam = camera_dict("persp", 22, 18, eye=eye, fwd=np.array([0.5, 0.5, 0.5]) - eye, up=(0, 0, 1),
+                          fov_y_deg=55.0)
+    a = oracle.render(pos, N, cam)
+    b = bf.render_barycentric(pos, N, cam)
+    c = bf.render_cell_projection(pos, N, cam)
+    assert a.max() > 0
+    np.testing.assert_allclose(a, b, atol=1e-12 * a.max())
+    np.testing.assert_allclose(a, c, atol=1e-9 * a.max())
+
+
+def test_oracle_matches_bruteforce_periodic_window():
+    N = 3
+    f = ZeldovichField.generate(N, -2.0, 1.5, 5)
+    pos = f.positions(1.2)
+    cam = offset_window(18, 16, off=(0.017, 0.029))
+    a = oracle.render(pos, N, cam)
+    b = bf.render_barycentric(pos, N, cam)
+    np.testing.assert_allclose(a, b, atol=1e-12 * a.max())
+
+
+# ---------------------------------------------------------------------------
+# Gradient
+
+
+def _fd_grad(pos, N, cam, target, comps, h=1e-6):
+    def loss(p):
+        img = oracle.render(p, N, cam)
+        return float(np.sum((img - target) ** 2))
+
+    base = pos[:, :3].astype(np.float64)
+    out = []
+    for (pid, a) in comps:
+        pp = base.copy()
+        pp[pid, a] += h
+        lp = loss(pp)
+        pp[pid, a] -= 2 * h
+        lm = loss(pp)
+        out.append((lp - lm) / (2 * h))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("view", ["ortho", "persp"])
+def test_gradient_matches_central_differences(view):
+    N = 3
+    f = ZeldovichField.generate(N, -2.0, 1.5, 9)
+    pos = f.positions(1.4).astype(np.float64)
+    if view == "ortho":
+        cam = camera_dict("ortho", 26, 22, fwd=(0.15, -0.1, 1.0), up=(0, 1, 0), lo=(-0.1, -0.1),
+                          hi=(1.1, 1.1), wrap=False)
+    else:
+        eye = np.array([1.9, 0.2, 1.4])
+        cam = camera_dict("persp", 24, 20, eye=eye, fwd=np.array([0.5, 0.5, 0.5]) - eye, up=(0, 0, 1),
+                          fov_y_deg=60.0)
+    rng = np.random.default_rng(3)
+    img = oracle.render(pos, N, cam)
+    target = img + rng.normal(0, 0.3, img.shape)
+    g = oracle.gradient(pos, N, cam, 2 * (img - target))
+    comps = [(p, a) for p in range(N ** 3) for a in range(3)]
+    fd = _fd_grad(pos, N, cam, target, comps)
+    an = np.array([g[p, a] for (p, a) in comps])
+    assert np.linalg.norm(an - fd) <= 1e-4 * np.linalg.norm(fd)
+
+
+def test_gradient_along_orthographic_axis_vanishes():
+    """Moving a vertex along the line of sight moves no mass between columns,
+    so dI/dz = 0 for a projection along z."""
+    N = 4
+    f = ZeldovichField.generate(N, -2.0, 2.0, 13)
+    pos = f.positions(1.6)
+    cam = offset_window(32, 32)
+    rng = np.random.default_rng(4)
+    g = oracle.gradient(pos, N, cam, rng.normal(size=(32, 32)))
+    assert np.abs(g[:, :2]).max() > 1e-3
+    assert np.abs(g[:, 2]).max() <= 1e-10 * np.abs(g[:, :2]).max()
