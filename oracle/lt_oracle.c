@@ -208,18 +208,22 @@ static void shift_range(long a, long b, long lo, long hi, long period, int wrap,
 }
 
 /* Pixel bounding box of a tetrahedron: pixels whose centres lie inside the
- * bounding box of the projected vertices. Returns 0 when the tetrahedron
- * cannot be projected (a vertex at or behind the perspective eye). */
+ * bounding box of the projected vertices. Returns 1 on success, 0 when the
+ * tetrahedron lies entirely behind a perspective eye (no ray reaches it; the
+ * box is empty), -1 when it straddles the eye plane (cannot be projected). */
 static int tet_pixel_box(const frame_t* fr, double v[4][3], long* x0, long* x1, long* y0, long* y1) {
   double mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+  int behind = 0;
   for (int c = 0; c < 4; ++c) {
     double fx, fy;
-    if (!to_pixel(fr, v[c], &fx, &fy)) return 0;
+    if (!to_pixel(fr, v[c], &fx, &fy)) { ++behind; continue; }
     if (fx < mnx) mnx = fx;
     if (fx > mxx) mxx = fx;
     if (fy < mny) mny = fy;
     if (fy > mxy) mxy = fy;
   }
+  if (behind == 4) { *x0 = 1; *x1 = 0; *y0 = 1; *y1 = 0; return 0; }
+  if (behind) return -1;
   *x0 = (long)ceil(mnx); *x1 = (long)floor(mxx);
   *y0 = (long)ceil(mny); *y1 = (long)floor(mxy);
   return 1;
@@ -276,7 +280,7 @@ int orc_render(const double* pos, int N, double box, double total_mass, const or
         if (V == 0.0) { degen[tid]++; continue; }
         double rho = m / fabs(V); /* Eq. 3 */
         long bx0, bx1, by0, by1;
-        if (!tet_pixel_box(&fr, v, &bx0, &bx1, &by0, &by1)) { errs[tid] = ORC_ERR_BEHIND_EYE; continue; }
+        if (tet_pixel_box(&fr, v, &bx0, &bx1, &by0, &by1) < 0) { errs[tid] = ORC_ERR_BEHIND_EYE; continue; }
         if (bx0 > bx1 || by0 > by1) continue;
         for (int c = 0; c < ncrops; ++c) {
           long cx0 = crops[4 * c], cy0 = crops[4 * c + 1];
@@ -407,7 +411,7 @@ int orc_grad(const double* pos, int N, double box, double total_mass, const orc_
           ids[cc] = ii + (long)N * (jj + (long)N * kk);
         }
         long bx0, bx1, by0, by1;
-        if (!tet_pixel_box(&fr, v, &bx0, &bx1, &by0, &by1)) { errs[tid] = ORC_ERR_BEHIND_EYE; continue; }
+        if (tet_pixel_box(&fr, v, &bx0, &bx1, &by0, &by1) < 0) { errs[tid] = ORC_ERR_BEHIND_EYE; continue; }
         if (bx0 > bx1 || by0 > by1) continue;
         long sx0, sx1, sy0, sy1;
         shift_range(bx0, bx1, 0, fr.W - 1, fr.W, fr.wrap, &sx0, &sx1);
@@ -493,7 +497,9 @@ int orc_render_soup(const double* verts /* [n][4][3] */, const double* dens, lon
     double v[4][3];
     memcpy(v, verts + 12 * t, sizeof v);
     long x0, x1, y0, y1;
-    if (!tet_pixel_box(&fr, v, &x0, &x1, &y0, &y1)) return ORC_ERR_BEHIND_EYE;
+    const int pb = tet_pixel_box(&fr, v, &x0, &x1, &y0, &y1);
+    if (pb < 0) return ORC_ERR_BEHIND_EYE;
+    if (pb == 0) continue;
     if (x0 < 0) x0 = 0;
     if (y0 < 0) y0 = 0;
     if (x1 > fr.W - 1) x1 = fr.W - 1;
