@@ -1,0 +1,415 @@
+"""Benchmark of the column-density projection on the headline workload.
+
+Workload (zel256_persp2048x128): a 256^3 particle lattice (100.7M
+tetrahedra per snapshot), 8 Zel'dovich snapshots with maximum deformation
+eigenvalue 0.5 .. 6, 16 perspective cameras on a sphere of radius 2 around
+the box (60 degree field of view), 2048 x 2048 pixels: 128 frames per step,
+rendered by one replay of a CUDA graph holding the project-and-bin pass and
+the persistent tile raster. Inputs are synthetic and seeded; the positions
+(2.1 GB) are larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0). `value` is fragments/s over the whole job: a
+fragment is a (tetrahedron, pixel) pair with a positive chord, counted once
+on the GPU for the workload (the counter is checked against the oracle in
+the tests). `--impl reference` times the FP64 CPU oracle instead, on bounded
+samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "tet-pixel fragments/s and frames/s at 256^3 particles, 2048^2 px vs plain atomic form"
+WORKLOAD = "zel256_persp2048x128"
+# FP32 operations per fragment in the raster's inner loop (FFMA counted as 2):
+# perspective: 4 edge FFMA + 3 min + 1 clamp + 2 depth-plane FFMA + 1 max +
+# 1 FFMA + 1 FMUL + 1 reciprocal-multiply = 22
+FLOPS_PER_FRAGMENT_PERSP = 22
+FLOPS_PER_FRAGMENT_ORTHO = 12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lt", choices=["lt", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--frames", type=int, default=0, help="override frame count (debug)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-atomic", action="store_true")
+    ap.add_argument("--cpu-sample-crop", type=int, default=384)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload
+
+
+def make_workload(name: str, frames_override: int = 0):
+    from lt_inputs import ZeldovichField, config, ortho_z, sphere_cameras
+
+    c = config(name)
+    N = c["N"]
+    f = ZeldovichField.generate(N, c["n_index"], c["k_cut"], c["seed"])
+    lams = c["lams"]
+    import numpy as np
+
+    pos = np.empty((len(lams), N ** 3, 4), dtype=np.float32)
+    for s, lam in enumerate(lams):
+        pos[s] = f.positions(lam)
+    if c["view"] == "sphere16":
+        cams0 = sphere_cameras(16, c["W"], c["H"], radius=c["radius"], fov_y_deg=c["fov_y_deg"])
+        cams, snaps = [], []
+        for s in range(len(lams)):
+            for cam in cams0:
+                cams.append(cam)
+                snaps.append(s)
+    else:
+        cams, snaps = [ortho_z(c["W"], c["H"])], [0]
+    if frames_override:
+        cams, snaps = cams[:frames_override], snaps[:frames_override]
+    return c, pos, cams, snaps
+
+
+# ---------------------------------------------------------------------------
+# clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = os.path.join(tempfile.gettempdir(), f"lt_clocks_{os.getpid()}.csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+
+def run_lt(args, rank: int, world: int):
+    import numpy as np
+    import torch
+
+    from paper_1208_3206_gb300.render import Renderer
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    c, pos_np, cams, snaps = make_workload(args.workload, args.frames)
+    N = c["N"]
+    F = len(cams)
+    W, H = cams[0]["W"], cams[0]["H"]
+    persp = cams[0]["type"] == "persp"
+
+    R = Renderer()
+    pos = torch.from_numpy(pos_np).to(dev)
+    R.build_tets(pos, N)
+    R.sync()
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        # autotune the tile size and CTA shape on a subset of the frames
+        tune_frames = list(range(0, F, max(1, F // 8)))
+        best = R.autotune([cams[q] for q in tune_frames], [snaps[q] for q in tune_frames], reps=1)
+        R.project_bin(cams, snaps)
+        frags = R.count_fragments()
+        stats_bin = R.get_stats()
+        img = torch.empty((F, H, W), dtype=torch.float32, device=dev)
+        mass = torch.empty(F, dtype=torch.float64, device=dev)
+        R.graph_build(cams, snaps, image=img, mass=mass, stream=stream)
+        R.sync()
+    total_frags = int(sum(frags))
+    gstats = R.get_stats()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            R.graph_launch(stream)
+    stream.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            R.graph_launch(stream)
+    e1.record(stream)
+    stream.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    R.sync()
+
+    # raster kernel alone (the dominant kernel), timed with events on its stream
+    with torch.cuda.stream(stream):
+        R.project_bin(cams, snaps)
+        R.render_tiles(image=img)
+        stream.synchronize()
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        reps = max(2, min(args.steps, 5))
+        r0.record(stream)
+        for _ in range(reps):
+            R.render_tiles(image=img)
+        r1.record(stream)
+        stream.synchronize()
+    raster_ms = r0.elapsed_time(r1) / reps
+    R.sync()
+
+    # end to end through the public API: pinned host positions in, images out
+    host_pos = torch.from_numpy(pos_np).pin_memory()
+    host_img = torch.empty((F, H, W), dtype=torch.float32).pin_memory()
+    e2e_steps = max(2, min(args.steps, 3))
+    with torch.cuda.stream(stream):
+        pos.copy_(host_pos, non_blocking=True)
+        R.graph_launch(stream)
+        host_img.copy_(img, non_blocking=True)
+        stream.synchronize()
+        barrier()
+        x0 = torch.cuda.Event(enable_timing=True)
+        x1 = torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        for _ in range(e2e_steps):
+            pos.copy_(host_pos, non_blocking=True)
+            R.graph_launch(stream)
+            host_img.copy_(img, non_blocking=True)
+        x1.record(stream)
+        stream.synchronize()
+    e2e_ms = x0.elapsed_time(x1) / e2e_steps
+    R.sync()
+
+    # plain one-cube-per-thread atomic form on the same frames, same arithmetic
+    atomic = None
+    if not args.no_atomic:
+        with torch.cuda.stream(stream):
+            a_img = torch.empty((F, H, W), dtype=torch.float32, device=dev)
+            R.render_atomic(cams, snaps, image=a_img)
+            stream.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            R.render_atomic(cams, snaps, image=a_img)
+            a1.record(stream)
+            stream.synchronize()
+        a_ms = a0.elapsed_time(a1)
+        diff = (a_img - img).abs().max().item()
+        ref_scale = max(img.mean().item(), 1e-30)
+        atomic = {"value": total_frags / (a_ms * 1e-3), "unit": "fragments/s", "ms_per_step": a_ms,
+                  "max_abs_diff_vs_tiled": diff, "max_rel_diff_vs_mean": diff / ref_scale}
+        del a_img
+        R.sync()
+
+    # max over ranks
+    if world > 1:
+        t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+
+    import torch.cuda as tc
+    props = tc.get_device_properties(dev)
+    sms = props.multi_processor_count
+    flops_per_frag = FLOPS_PER_FRAGMENT_PERSP if persp else FLOPS_PER_FRAGMENT_ORTHO
+    peak_clock_mhz = 2070.0
+    peak = sms * 128 * 2 * peak_clock_mhz * 1e6 / 1e12  # TFLOP/s FP32 at the maximum SM clock
+    achieved = total_frags * flops_per_frag / (raster_ms * 1e-3) / 1e12
+
+    value = world * total_frags / (ms * 1e-3)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "fragments/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": args.workload,
+            "particles": N ** 3,
+            "tets_per_snapshot": 6 * N ** 3,
+            "snapshots": len(set(snaps)),
+            "frames": F,
+            "image": [W, H],
+            "fragments_per_step": total_frags,
+            "bin_entries": stats_bin["entries"],
+            "tile": best.get("tile"),
+            "raster_threads": best.get("raster_threads"),
+            "l2": "inputs larger than L2 (positions %.2f GB)" % (pos.numel() * 4 / 1e9),
+            "graph": "one CUDA graph replay per step (project-and-bin + persistent tile raster)",
+        },
+        "frames_per_s": world * F / (ms * 1e-3),
+        "gpu_launches": int(gstats["graph_kernels"]) * args.steps,
+        "clocks": clk,
+        "roofline": {
+            "bound": "alu",
+            "kernel": "k_raster (persistent tile raster)",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "traffic": None,
+            "counted": f"{flops_per_frag} FP32 flops per fragment",
+            "peak_from": f"{sms} SMs x 128 FP32 lanes x 2 x {peak_clock_mhz:.0f} MHz",
+            "raster_ms": raster_ms,
+        },
+        "e2e": {
+            "value": world * total_frags / (e2e_ms * 1e-3),
+            "unit": "fragments/s",
+            "ms_per_step": e2e_ms,
+            "h2d_bytes_per_step": int(pos.numel() * 4),
+            "d2h_bytes_per_step": int(img.numel() * 4),
+        },
+    }
+    if atomic is not None:
+        line["atomic"] = atomic
+        line["tiled_over_atomic"] = atomic["ms_per_step"] / ms
+    return line, (c, pos_np, cams, snaps)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle
+
+
+def oracle_sample(c, pos_np, cams, snaps, crop: int, frame: int = 0):
+    """Time the FP64 oracle on one crop of one frame; returns (fragments, seconds)."""
+    import oracle
+
+    N = c["N"]
+    cam = cams[frame]
+    s = snaps[frame]
+    W, H = cam["W"], cam["H"]
+    x0, y0 = (W - crop) // 2, (H - crop) // 2
+    t = time.perf_counter()
+    _, nf, _ = oracle.render_crops(pos_np[s], N, cam, [(x0, y0, crop, crop)])
+    return nf, time.perf_counter() - t
+
+
+def cpu_baseline(c, pos_np, cams, snaps, crop: int):
+    nf, sec = oracle_sample(c, pos_np, cams, snaps, crop)
+    cores = os.cpu_count()
+    return {"value": nf / sec, "unit": "fragments/s", "cores": cores, "kind": "oracle",
+            "sample": f"frame 0, central {crop}x{crop} crop ({nf} fragments, {sec:.1f} s incl. the scan of all "
+                      f"{6 * c['N'] ** 3} tetrahedra)"}
+
+
+def run_reference(args, rank: int, world: int):
+    c, pos_np, cams, snaps = make_workload(args.workload, args.frames)
+    if rank != 0:
+        return None
+    # each step: one bounded sample of the same workload (a central crop of
+    # one frame), rotating through the frames
+    for w in range(args.warmup):
+        oracle_sample(c, pos_np, cams, snaps, min(64, args.cpu_sample_crop), w % len(cams))
+    tot_f, tot_s = 0, 0.0
+    for st in range(args.steps):
+        nf, sec = oracle_sample(c, pos_np, cams, snaps, args.cpu_sample_crop, st % len(cams))
+        tot_f += nf
+        tot_s += sec
+    value = tot_f / tot_s
+    cores = os.cpu_count()
+    sample = f"per step one central {args.cpu_sample_crop}^2 crop of one frame ({tot_f // max(1, args.steps)} fragments)"
+    return {
+        "metric": METRIC, "value": value, "unit": "fragments/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": args.workload, "particles": c["N"] ** 3, "frames": len(cams),
+                   "image": [cams[0]["W"], cams[0]["H"]]},
+        "cpu_baseline": {"value": value, "unit": "fragments/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "fragments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "lt" else "gloo"
+        if args.impl == "lt":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend=backend)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line, wl = run_lt(args, rank, world)
+        if rank == 0 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(*wl, crop=args.cpu_sample_crop)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * lt.h -- C ABI of the GB300 column-density renderer for the Lagrangian
+ * tetrahedral tessellation of a periodic particle lattice
+ * (Kaehler, Hahn & Abel, "A Novel Approach to Visualizing Dark Matter
+ * Simulations", arXiv:1208.3206).
+ *
+ * What the library computes (Sec. 3.2, Eq. 6 with the density of Eq. 3):
+ * for every pixel of every requested frame,
+ *
+ *     I(pixel) = sum over tetrahedra t of rho_t * dl_t(pixel),
+ *
+ * rho_t = m / |V_t| the constant density of tetrahedron t (V_t from Eq. 9),
+ * m = total_mass / (6 N^3), and dl_t(pixel) the length of the ray through the
+ * pixel centre inside t. The tetrahedra are the six per cube of the initial
+ * N^3 particle lattice (Sec. 3.1, connectivity table of Sec. 4.1), built on
+ * the fly from the particle id <-> lattice index map (Eq. 8); no
+ * connectivity is stored.
+ *
+ * Conventions shared by every entry point:
+ *   - Device pointers are CUDA device memory owned by the caller; the
+ *     library never frees or keeps a pointer it did not allocate, except the
+ *     position buffer registered by lt_build_tets, which must stay valid and
+ *     unchanged in shape until the next lt_build_tets or lt_destroy.
+ *   - Host pointers are read during the call only.
+ *   - Calls are asynchronous on the given stream (0 = legacy default
+ *     stream) unless stated otherwise. Errors the device detects (capacity
+ *     overflow, non-finite positions, vertices behind a perspective eye,
+ *     accumulator range) are latched in the context and returned by the next
+ *     synchronising call (lt_get_stats, lt_sync).
+ *   - Every function returns an lt_status and never aborts the process.
+ *   - A context is used by one host thread at a time.
+ *
+ * Layouts:
+ *   - positions, LT_POS_F32X4: float4 (x, y, z, unused) per particle, id
+ *     order i + N (j + N k) (Eq. 8), wrapped into [0, box)^3; n_snapshots
+ *     arrays of N^3 particles back to back.
+ *   - positions, LT_POS_F16_OFFSETS: 4 halves (dx, dy, dz, unused) per
+ *     particle, the displacement from the particle's lattice point in units
+ *     of the lattice spacing box / N (not wrapped).
+ *   - images: float [n_frames][H][W], row py along the camera's up axis,
+ *     pixel (px, py) centred at ((px + 1/2) / W, (py + 1/2) / H) of the view.
+ *   - tetrahedron id: 6 * (i + N (j + N k)) + s, s the row of the
+ *     connectivity table of Sec. 4.1 for cube (i, j, k).
+ */
+#ifndef LT_H_
+#define LT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* lt_stream; /* a cudaStream_t */
+
+typedef enum {
+  LT_OK = 0,
+  LT_ERR_ARG = 1,         /* invalid argument: null pointer, bad size or enum */
+  LT_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  LT_ERR_CAPACITY = 3,    /* a bin list outgrew its reserved capacity */
+  LT_ERR_NONFINITE = 4,   /* a particle position is NaN or infinite */
+  LT_ERR_BEHIND_EYE = 5,  /* a perspective frame has a vertex at or behind the eye plane */
+  LT_ERR_RANGE = 6,       /* a pixel exceeded the fixed-point accumulator range */
+  LT_ERR_STATE = 7,       /* calls made out of order (e.g. render before bin) */
+  LT_ERR_NOMEM = 8        /* device allocation failed */
+} lt_status;
+
+typedef enum { LT_POS_F32X4 = 0, LT_POS_F16_OFFSETS = 1 } lt_pos_format;
+typedef enum { LT_ORTHO = 0, LT_PERSP = 1 } lt_camera_type;
+
+/* One view. right = normalize(up x fwd), up' = fwd x right.
+ * LT_ORTHO: rays along fwd through the window [lo, hi] of the (right, up')
+ *   coordinates of world points; wrap != 0 makes the window periodic (every
+ *   periodic copy of a tetrahedron is drawn; use a window one box wide).
+ * LT_PERSP: rays from eye; vertical field of view fov_y_deg, square pixels;
+ *   every vertex must lie in front of the eye (LT_ERR_BEHIND_EYE).
+ * The view is set up in double precision on the host; each cube's projected
+ * anchor point is carried to the kernels with about 2^-37 relative error, so
+ * pixel positions are exact to well below a millionth of a pixel. */
+typedef struct {
+  int type;
+  double eye[3];
+  double fwd[3];
+  double up[3];
+  double fov_y_deg;
+  double lo[2];
+  double hi[2];
+  int W, H;
+  int wrap;
+} lt_camera;
+
+/* Tuning knobs (lt_autotune fills them; zero fields take defaults). */
+typedef struct {
+  int tile;           /* screen tile edge in pixels: 8, 16, 32 or 64 (default 16) */
+  int raster_threads; /* threads per raster CTA: 64..1024, multiple of 32 (default 256) */
+  int ctas_per_sm;    /* persistent raster CTAs per SM (default: occupancy limit) */
+  int frac_bits;      /* fixed-point fraction bits relative to the mean column density (default 28) */
+} lt_config;
+
+typedef struct {
+  long long tets;            /* tetrahedra per snapshot, 6 N^3 */
+  long long entries;         /* (tile, cube) bin entries of the last lt_project_bin */
+  long long capacity;        /* reserved bin entries */
+  long long degenerate;      /* tetrahedra with V == 0 found by lt_build_tets */
+  long long fp64_fallbacks;  /* volumes recomputed in FP64 by lt_build_tets */
+  long long inverted;        /* tetrahedra with V > 0 (orientation flipped vs t = 0) */
+  long long nonfinite;       /* non-finite positions seen */
+  long long behind_eye;      /* cubes skipped because a vertex is behind the eye */
+  long long range_overflow;  /* pixels that left the accumulator range */
+  int n_frames;              /* frames of the last lt_project_bin */
+  int tile;                  /* tile edge in use */
+  int graph_kernels;         /* kernel nodes in the graph of the last lt_graph_build */
+  int pad;
+} lt_stats;
+
+typedef struct lt_ctx lt_ctx;
+
+/* Create a context bound to the current CUDA device. cfg may be NULL.
+ * Ownership: the context owns every scratch buffer it allocates (bins,
+ * offsets, work queue, counters); lt_destroy frees them. */
+lt_status lt_create(lt_ctx** out, const lt_config* cfg);
+void lt_destroy(lt_ctx* ctx);
+
+/* Replace the tuning knobs (takes effect at the next lt_project_bin). */
+lt_status lt_set_config(lt_ctx* ctx, const lt_config* cfg);
+lt_status lt_get_config(const lt_ctx* ctx, lt_config* out);
+
+/*
+ * lt_build_tets -- Sec. 3.1 / Sec. 4.1 (tessellation and per-tetrahedron
+ * volume and density, Eq. 8, 9 and 3).
+ * Registers n_snapshots position arrays at d_pos (layout above, caller
+ * owned, read by every later call) for a lattice of N^3 particles in a
+ * periodic box of edge `box` holding `total_mass`. Checks every position
+ * for finiteness and computes, for every tetrahedron of every snapshot, the
+ * signed volume V (FP32 from displacement differences, recomputed in FP64
+ * when |V| < 0.1 of a lattice cell, where the FP32 error bound would pass
+ * 1e-5; this covers every near-degenerate sheet tetrahedron at caustics) and
+ * rho = m / |V| (0 when V == 0). If d_rho is not NULL it
+ * receives rho as float [n_snapshots][6 N^3] (tetrahedron id order).
+ * Errors: LT_ERR_ARG (N < 1, N^3 > 2^31, box <= 0, total_mass <= 0,
+ * n_snapshots < 1, unknown pos_fmt, misaligned d_pos); non-finite positions
+ * latch LT_ERR_NONFINITE.
+ */
+lt_status lt_build_tets(lt_ctx* ctx, const void* d_pos, int pos_fmt, int N, float box, double total_mass,
+                        int n_snapshots, float* d_rho, lt_stream stream);
+
+/*
+ * lt_project_bin -- project-and-bin pass (the screen-space counterpart of
+ * the rasterisation step of Sec. 4.4).
+ * For each of n_frames views cams[f] (host array) of snapshot
+ * frame_snapshot[f] (host array, NULL = snapshot 0 for every frame), bins
+ * every lattice cube into the screen tiles its projected bounding box
+ * overlaps: warp-aggregated per-tile counts, a device exclusive scan, then a
+ * scatter of cube ids into per-tile lists. Also orders the (frame, tile) work
+ * items by descending list length for the raster pass.
+ * Outside stream capture the call synchronises once to size the lists
+ * (growing the context's buffers as needed). Inside stream capture it uses
+ * the reserved capacity and latches LT_ERR_CAPACITY if it is exceeded.
+ * Errors: LT_ERR_STATE (no lt_build_tets), LT_ERR_ARG (n_frames < 1, bad
+ * camera, snapshot out of range, W or H < 1 or > 65536).
+ */
+lt_status lt_project_bin(lt_ctx* ctx, const lt_camera* cams, int n_frames, const int* frame_snapshot,
+                         lt_stream stream);
+
+/*
+ * lt_render_tiles -- the projection of Eq. 6 for every frame of the last
+ * lt_project_bin. One persistent launch; each CTA takes (frame, tile) work
+ * items, accumulates rho_t * dl_t of every tetrahedron of the tile's cubes
+ * into on-chip fixed-point integer sums (so the image is bit-reproducible
+ * whatever the order), and stores every pixel once.
+ * d_image: float [n_frames][H][W] (caller owned). d_mass (may be NULL):
+ * double [n_frames], per frame the sum of pixel values times the pixel area
+ * (orthographic: window area / (W H); perspective: area on the image plane
+ * at unit distance), reduced in a fixed order.
+ * Errors: LT_ERR_STATE (no lt_project_bin), LT_ERR_ARG (null d_image).
+ */
+lt_status lt_render_tiles(lt_ctx* ctx, float* d_image, double* d_mass, lt_stream stream);
+
+/*
+ * lt_render_atomic -- the plain form of Eq. 6: one thread per lattice cube
+ * over all frames, every fragment added to the image with a float atomic
+ * (order dependent in the last bits). Same arithmetic per tetrahedron as
+ * lt_render_tiles; it needs no bins. d_image must be zeroed by the caller.
+ * Errors: LT_ERR_STATE (no lt_build_tets), LT_ERR_ARG.
+ */
+lt_status lt_render_atomic(lt_ctx* ctx, const lt_camera* cams, int n_frames, const int* frame_snapshot,
+                           float* d_image, lt_stream stream);
+
+/*
+ * lt_count_fragments -- number of (tetrahedron, pixel) pairs with a positive
+ * chord in each frame of the last lt_project_bin (the work unit of the
+ * benchmark). Synchronises; h_counts: host long long [n_frames].
+ */
+lt_status lt_count_fragments(lt_ctx* ctx, long long* h_counts, lt_stream stream);
+
+/*
+ * lt_render_backward -- adjoint of lt_render_tiles (the derivative of
+ * Eq. 6 with respect to particle positions). Given dL/dI as float
+ * [n_frames][H][W] for the frames of the last lt_project_bin, writes
+ * dL/d(position) as float [n_snapshots][N^3][3] into d_dL_dpos (overwritten,
+ * caller owned). Deterministic: per-tetrahedron gradients are gathered per
+ * particle in a fixed order, no float atomics.
+ * Errors: LT_ERR_STATE, LT_ERR_ARG.
+ */
+lt_status lt_render_backward(lt_ctx* ctx, const float* d_dL_dimage, float* d_dL_dpos, lt_stream stream);
+
+/*
+ * lt_graph_build / lt_graph_launch -- capture lt_project_bin followed by
+ * lt_render_tiles for the given frames into a CUDA graph owned by the
+ * context, and replay it. lt_graph_build runs the pass once uncaptured to
+ * size the bins (reserving 25 % headroom), then captures on `stream`.
+ * Replays re-read the registered positions, so new snapshot contents
+ * (same shape) may be written between launches. Capacity overflow during a
+ * replay latches LT_ERR_CAPACITY.
+ */
+lt_status lt_graph_build(lt_ctx* ctx, const lt_camera* cams, int n_frames, const int* frame_snapshot,
+                         float* d_image, double* d_mass, lt_stream stream);
+lt_status lt_graph_launch(lt_ctx* ctx, lt_stream stream);
+
+/*
+ * lt_autotune -- time lt_project_bin + lt_render_tiles for the given
+ * frames over a small grid of tile sizes and raster CTA shapes (CUDA
+ * events, `reps` timed repetitions each after one warm-up), keep the
+ * fastest in the context and report it in *best (may be NULL).
+ * Synchronises. d_image: scratch float [n_frames][H][W].
+ */
+lt_status lt_autotune(lt_ctx* ctx, const lt_camera* cams, int n_frames, const int* frame_snapshot,
+                      float* d_image, int reps, lt_config* best, lt_stream stream);
+
+/* Wait for the stream, then return (and clear) the first latched device error. */
+lt_status lt_sync(lt_ctx* ctx, lt_stream stream);
+
+/* Synchronise and read counters; returns the first latched error (and clears it). */
+lt_status lt_get_stats(lt_ctx* ctx, lt_stats* out);
+
+/* Static string for a status code. */
+const char* lt_status_str(lt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LT_H_ */

@@ -1,0 +1,529 @@
+// lt_common.cuh -- device-side building blocks shared by every kernel of the
+// column-density renderer: lattice addressing, cube projection and the
+// per-tetrahedron form of rho_t * dl_t used by the raster passes.
+//
+// The projection of Eq. 6 (Sec. 3.2) adds rho_t * dl_t(ray) for every
+// tetrahedron t, rho_t = m / |V_t| (Eq. 3, 9). For a straight ray, dl_t is
+// piecewise linear across the image and |V_t| cancels:
+//
+//  * Orthographic view. dl_t(x) / |V_t| is a pyramid over the convex hull of
+//    the four projected vertices with unit integral: apex at the projected
+//    vertex that lies inside the triangle of the other three, or at the
+//    crossing of the two projected diagonals, apex height 3 / area(hull).
+//    So rho_t * dl_t(x) = m * pyramid(x): only the projected vertex positions
+//    enter. In pixel units the pyramid is min over hull edges (j,k) of
+//        6 m * orient(v_j, v_k, x) / (orient(v_j, v_k, v_l1) * orient(v_j, v_k, v_l2)),
+//    {l1, l2} the other two vertices (orient = 2D signed double area).
+//  * Perspective view. Under (X, Y, Z) -> (X/Z, Y/Z, 1/Z) planes stay planes
+//    and every ray becomes a line of constant image position, so the ray
+//    parameter interval [1/w_hi, 1/w_lo] is the w-extent of the mapped
+//    tetrahedron, whose volume is |V| / (Z0 Z1 Z2 Z3). Hence
+//        rho_t * dl_t = m kx ky |d| pyramid'(x) / (Z0 Z1 Z2 Z3 * w_lo * w_hi),
+//    pyramid' the same construction on the perspective-projected vertices,
+//    |d| the length of the pixel's ray direction (x, y, 1). w_lo and w_hi
+//    are the lower and upper depth surfaces of the mapped tetrahedron.
+//
+// Both are exact rewritings of rho * dl (no approximation); the volume is
+// never divided by, which keeps sheet-like tetrahedra at caustics well
+// conditioned in FP32.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lt {
+
+// Connectivity of the six tetrahedra of a cube (Sec. 4.1); corner n of cube
+// (i, j, k) is lattice point (i + (n & 1), j + ((n >> 1) & 1), k + ((n >> 2) & 1)).
+__host__ __device__ constexpr int tet_corner(int s, int c) {
+  return (s == 0) ? (c == 0 ? 1 : c == 1 ? 0 : c == 2 ? 2 : 4)
+       : (s == 1) ? (c == 0 ? 3 : c == 1 ? 1 : c == 2 ? 2 : 4)
+       : (s == 2) ? (c == 0 ? 3 : c == 1 ? 5 : c == 2 ? 1 : 4)
+       : (s == 3) ? (c == 0 ? 3 : c == 1 ? 6 : c == 2 ? 5 : 4)
+       : (s == 4) ? (c == 0 ? 3 : c == 1 ? 2 : c == 2 ? 6 : 4)
+                  : (c == 0 ? 3 : c == 1 ? 7 : c == 2 ? 5 : 6);
+}
+
+// Latched device error bits (combined with atomicOr).
+enum : unsigned {
+  kErrCapacity = 1u,
+  kErrNonFinite = 2u,
+  kErrBehindEye = 4u,
+  kErrRange = 8u,
+};
+
+// Device counters, one block of them per context.
+struct DevCounters {
+  unsigned errors;
+  unsigned pad;
+  unsigned long long nonfinite;
+  unsigned long long behind_eye;
+  unsigned long long degenerate;
+  unsigned long long fp64_fallbacks;
+  unsigned long long inverted;
+  unsigned long long range_overflow;
+  unsigned long long work_next;   // persistent raster work counter
+  unsigned long long total_entries;
+};
+
+// Snapshot description.
+struct Lattice {
+  const void* pos;  // float4 or half4 per particle, n_snap arrays back to back
+  int fmt;          // 0 float4 wrapped positions, 1 half4 offsets in cell units
+  int N;
+  float box, h, half_box;
+  long long n_particles;  // N^3
+};
+
+// One view in kernel form.
+struct FrameDev {
+  int persp, W, H, wrap;
+  int snapshot, tiles_x, tiles_y, tile;
+  long long tile_base;  // first global tile index of this frame
+  float r[3], u[3], f[3], eye[3];
+  float sx, sy, ox, oy;   // ortho: pixel = dot(axis, P) * s + o
+  float kx, ky, cx, cy;   // persp: pixel = (X / Z) * k + c in camera coordinates
+  float near_z;           // perspective: vertices must have Z > near_z
+  // Projected position of cube (i, j, k)'s Lagrangian corner as an affine
+  // function of the lattice index, component c = ah[c][0] + i ah[c][1] +
+  // j ah[c][2] + k ah[c][3] plus the same with al. The ah parts are integer
+  // multiples of one power of two that keep every partial sum below 2^24
+  // of it, so that sum is exact in FP32; al carries the remainder.
+  // Orthographic: c = 0, 1 are pixel coordinates. Perspective: camera X, Y, Z.
+  float ah[3][4], al[3][4];
+  float kxh, kxl, kyh, kyl;  // perspective pixel scales as float-float pairs
+  float K;                // value scale in accumulator units (see lt_api.cu)
+  float inv6K;            // 1 / (6 K)
+  float tan_x, tan_y;     // perspective image-plane half extents at unit distance
+  double unit;            // accumulator unit -> column density
+  double pix_area;        // pixel area for the frame mass
+};
+
+// ---------------------------------------------------------------------------
+// Lattice addressing (Eq. 8) and the unwrapped corner positions.
+
+__device__ __forceinline__ long long particle_id(int i, int j, int k, int N) {
+  return (long long)i + (long long)N * ((long long)j + (long long)N * k);
+}
+
+// Minimum-image displacement of a wrapped coordinate p from its wrapped
+// lattice point q (both in [0, box)). Each branch is a single FP32 subtraction
+// of operands within a factor of two of each other where it matters
+// (q +- box is exact for lattice points), so the displacement is the FP32
+// rounding of the exact value even for particles that crossed the periodic
+// boundary.
+__device__ __forceinline__ float min_image(float p, float q, float box, float half_box) {
+  const float d0 = p - q;
+  return d0 > half_box ? p - (q + box) : (d0 < -half_box ? p - (q - box) : d0);
+}
+
+// Displacement of the particle at corner n of cube (i, j, k) from its own
+// Lagrangian point. ok = false for non-finite data.
+__device__ __forceinline__ float3 load_disp(const Lattice& L, long long snap_off, int i, int j, int k, int n,
+                                            bool& ok) {
+  const int a = n & 1, b = (n >> 1) & 1, c = (n >> 2) & 1;
+  int ii = i + a, jj = j + b, kk = k + c;
+  const int N = L.N;
+  int im = ii == N ? 0 : ii, jm = jj == N ? 0 : jj, km = kk == N ? 0 : kk;
+  long long id = snap_off + particle_id(im, jm, km, N);
+  if (L.fmt == 0) {
+    float4 p = __ldg(reinterpret_cast<const float4*>(L.pos) + id);
+    const float dx = min_image(p.x, (float)im * L.h, L.box, L.half_box);
+    const float dy = min_image(p.y, (float)jm * L.h, L.box, L.half_box);
+    const float dz = min_image(p.z, (float)km * L.h, L.box, L.half_box);
+    ok = ok && isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
+    return make_float3(dx, dy, dz);
+  }
+  const uint2 raw = __ldg(reinterpret_cast<const uint2*>(L.pos) + id);
+  __half2 xy = *reinterpret_cast<const __half2*>(&raw.x);
+  __half2 zw = *reinterpret_cast<const __half2*>(&raw.y);
+  float2 fxy = __half22float2(xy);
+  float fz = __low2float(zw);
+  ok = ok && isfinite(fxy.x) && isfinite(fxy.y) && isfinite(fz);
+  return make_float3(fxy.x * L.h, fxy.y * L.h, fz * L.h);
+}
+
+// One corner of cube (i, j, k) as a local offset from the cube's Lagrangian
+// corner 0 (box units): lattice offset plus displacement.
+__device__ __forceinline__ float3 load_corner(const Lattice& L, long long snap_off, int i, int j, int k, int n,
+                                              bool& ok) {
+  const float3 d = load_disp(L, snap_off, i, j, k, n, ok);
+  const int a = n & 1, b = (n >> 1) & 1, c = (n >> 2) & 1;
+  return make_float3((float)a * L.h + d.x, (float)b * L.h + d.y, (float)c * L.h + d.z);
+}
+
+// The eight corners of a cube projected to pixel coordinates, relative to
+// the projection (ax, ay) of the cube's Lagrangian corner 0.
+struct CubeProj {
+  float x[8], y[8];
+  float dw[8];   // perspective: 1/Z_n - 1/Z_anchor
+  float z[8];    // perspective: Z_n (camera depth)
+  float axh, axl, ayh, ayl;  // anchor pixel coordinate as hi + lo
+  float w0;      // perspective: 1 / Z_anchor
+  float xmin, xmax, ymin, ymax;  // relative bounding box of the 8 corners
+};
+
+// Lattice-affine anchor component as (hi, lo); hi is exact (see FrameDev).
+__device__ __forceinline__ void anchor_affine(const FrameDev& F, int c, int i, int j, int k, float& hi, float& lo) {
+  hi = fmaf((float)k, F.ah[c][3], fmaf((float)j, F.ah[c][2], fmaf((float)i, F.ah[c][1], F.ah[c][0])));
+  lo = fmaf((float)k, F.al[c][3], fmaf((float)j, F.al[c][2], fmaf((float)i, F.al[c][1], F.al[c][0])));
+}
+
+// Float-float (Xh + Xl) / (Zh + Zl) * (kh + kl) + c0 -> (hi, lo).
+__device__ __forceinline__ void ff_project(float Xh, float Xl, float Zh, float Zl, float kh, float kl, float c0,
+                                           float& hi, float& lo) {
+  const float q = Xh / Zh;
+  float r = fmaf(-q, Zh, Xh);  // exact residual of the division
+  r = fmaf(-q, Zl, Xl) + r;
+  const float ql = r / Zh;
+  const float p = kh * q;
+  float e = fmaf(kh, q, -p);   // exact product error
+  e = fmaf(kh, ql, e);
+  e = fmaf(kl, q, e);
+  const float s = p + c0;      // two-sum of p and c0
+  const float bb = s - p;
+  const float err = (p - (s - bb)) + (c0 - bb);
+  hi = s;
+  lo = err + e;
+}
+
+// Pixel coordinate relative to a cube copy's anchor (exact to ~1e-9 px for
+// the pixel counts of one frame).
+__device__ __forceinline__ float rel_coord(int p, int shift, float ah, float al) {
+  return ((float)(p - shift) - ah) - al;
+}
+
+// Returns true when the cube can be drawn. A perspective cube entirely behind
+// the eye plane is culled (no ray reaches it); one straddling the plane
+// cannot be projected and sets straddle (callers count and report it).
+template <bool PERSP>
+__device__ __forceinline__ bool project_cube(const Lattice& L, const FrameDev& F, long long cube, CubeProj& P,
+                                             bool& finite_ok, bool* straddle = nullptr) {
+  const int N = L.N;
+  const int i = (int)(cube % N);
+  const int j = (int)((cube / N) % N);
+  const int k = (int)(cube / ((long long)N * N));
+  const long long snap_off = (long long)F.snapshot * L.n_particles;
+  bool ok = true;
+  if (!PERSP) {
+    anchor_affine(F, 0, i, j, k, P.axh, P.axl);
+    anchor_affine(F, 1, i, j, k, P.ayh, P.ayl);
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      float3 l = load_corner(L, snap_off, i, j, k, n, ok);
+      P.x[n] = (F.r[0] * l.x + F.r[1] * l.y + F.r[2] * l.z) * F.sx;
+      P.y[n] = (F.u[0] * l.x + F.u[1] * l.y + F.u[2] * l.z) * F.sy;
+    }
+  } else {
+    float Xh, Xl, Yh, Yl, Zh, Zl;
+    anchor_affine(F, 0, i, j, k, Xh, Xl);
+    anchor_affine(F, 1, i, j, k, Yh, Yl);
+    anchor_affine(F, 2, i, j, k, Zh, Zl);
+    const float X0 = Xh + Xl, Y0 = Yh + Yl, Z0 = Zh + Zl;
+    bool front = Z0 > F.near_z;
+    int n_front = front ? 1 : 0;
+    if (front) {
+      ff_project(Xh, Xl, Zh, Zl, F.kxh, F.kxl, F.cx, P.axh, P.axl);
+      ff_project(Yh, Yl, Zh, Zl, F.kyh, F.kyl, F.cy, P.ayh, P.ayl);
+    }
+    const float iZ0 = 1.0f / Z0;
+    P.w0 = iZ0;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) {
+      float3 l = load_corner(L, snap_off, i, j, k, n, ok);
+      const float dX = F.r[0] * l.x + F.r[1] * l.y + F.r[2] * l.z;
+      const float dY = F.u[0] * l.x + F.u[1] * l.y + F.u[2] * l.z;
+      const float dZ = F.f[0] * l.x + F.f[1] * l.y + F.f[2] * l.z;
+      const float Zn = Z0 + dZ;
+      front = front && (Zn > F.near_z);
+      n_front += Zn > F.near_z ? 1 : 0;
+      const float inv = 1.0f / (Zn * Z0);
+      // X_n/Z_n - X0/Z0 = (dX Z0 - X0 dZ) / (Z_n Z0), free of cancellation
+      P.x[n] = (dX * Z0 - X0 * dZ) * inv * F.kx;
+      P.y[n] = (dY * Z0 - Y0 * dZ) * inv * F.ky;
+      P.dw[n] = -dZ * inv;
+      P.z[n] = Zn;
+    }
+    if (!front) {
+      finite_ok = finite_ok && ok;
+      if (straddle) *straddle = ok && n_front > 0;
+      return false;
+    }
+  }
+  finite_ok = finite_ok && ok;
+  if (!ok) return false;
+  float xmn = P.x[0], xmx = P.x[0], ymn = P.y[0], ymx = P.y[0];
+#pragma unroll
+  for (int n = 1; n < 8; ++n) {
+    xmn = fminf(xmn, P.x[n]); xmx = fmaxf(xmx, P.x[n]);
+    ymn = fminf(ymn, P.y[n]); ymx = fmaxf(ymx, P.y[n]);
+  }
+  P.xmin = xmn; P.xmax = xmx; P.ymin = ymn; P.ymax = ymx;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Per-tetrahedron setup.
+
+struct TetRaster {
+  // value(X, Y) = max(0, min_e a[e] X + b[e] Y + c[e]) (ortho, accumulator units)
+  float a[4], b[4], c[4];
+  // perspective depth surface: M = max(pa0 X + pb0 Y + pc0, pa1 X + pb1 Y + pc1),
+  // value = T / (M (M + g T)), T the pyramid above
+  float pa[2], pb[2], pc[2];
+  float g;
+  float xmin, xmax, ymin, ymax;  // relative bounding box
+};
+
+__device__ __forceinline__ float cross2(float ax, float ay, float bx, float by) { return ax * by - ay * bx; }
+
+// Conditionally swap two scalars.
+__device__ __forceinline__ void cswap(bool s, float& p, float& q) {
+  const float tp = p, tq = q;
+  p = s ? tq : tp;
+  q = s ? tp : tq;
+}
+
+// One hull edge (j, k) with the other two vertices l1, l2, in canonical
+// coordinates; writes f_e = sigma * w * orient(v_j, v_k, x) with
+// w = W / |o1 o2| (W = 6 K, or 6 K / (Z0 Z1 Z2 Z3) in perspective).
+__device__ __forceinline__ void edge_fn(float xj, float yj, float ex, float ey, float o1, float o2, float Wn,
+                                        float tiny, float& a, float& b, float& c) {
+  const float prod = fmaxf(fabsf(o1 * o2), tiny);
+  float w = Wn / prod;
+  w = (o1 + o2) < 0.0f ? -w : w;
+  const bool dead = (o1 == 0.0f) && (o2 == 0.0f);  // zero-length edge or flat hull
+  a = dead ? 0.0f : -ey * w;
+  b = dead ? 0.0f : ex * w;
+  c = dead ? __int_as_float(0x7f800000) : (ey * xj - ex * yj) * w;
+}
+
+// Plane of the mapped face (p, q, r) in (X, Y, w) space, w relative to the anchor.
+__device__ __forceinline__ bool face_plane(float xp, float yp, float wp, float xq, float yq, float wq, float xr,
+                                           float yr, float wr, float& pa, float& pb, float& pc) {
+  const float ux = xq - xp, uy = yq - yp, uw = wq - wp;
+  const float vx = xr - xp, vy = yr - yp, vw = wr - wp;
+  const float nw = ux * vy - uy * vx;
+  const float nx = uy * vw - uw * vy;
+  const float ny = uw * vx - ux * vw;
+  if (nw == 0.0f) return false;
+  const float inw = 1.0f / nw;
+  pa = -nx * inw;
+  pb = -ny * inw;
+  pc = wp - pa * xp - pb * yp;
+  return true;
+}
+
+// Canonical labelling of a projected tetrahedron. The signed areas
+// c_i = (-1)^i orient(vertices other than i) sum to zero; same-sign pairs are
+// the diagonals of a convex quadrilateral hull (two of each sign, "case B"),
+// and a lone sign marks the vertex inside the triangle of the other three
+// ("case A"). Vertices are reordered so that the diagonals are (0,1) | (2,3),
+// or the inner vertex is 3.
+struct TetCanon {
+  float x[4], y[4], w[4];
+  int perm[4];                 // canonical position -> original vertex slot
+  bool caseB;
+  float d1x, d1y, d2x, d2y, d3x, d3y;
+  float D12, D13, D23, O123;   // orient(0,1,2), orient(0,1,3), orient(0,2,3), orient(1,2,3)
+  float S;                     // sum |c_i| = 4 * area(hull)
+};
+
+__device__ __forceinline__ void cswapi(bool s, int& p, int& q) {
+  const int tp = p, tq = q;
+  p = s ? tq : tp;
+  q = s ? tp : tq;
+}
+
+__device__ __forceinline__ bool tet_canon(float x0, float y0, float x1, float y1, float x2, float y2, float x3,
+                                          float y3, float w0, float w1, float w2, float w3, TetCanon& k) {
+  const float ax = x1 - x0, ay = y1 - y0, bx = x2 - x0, by = y2 - y0, cx = x3 - x0, cy = y3 - y0;
+  const float ab = cross2(ax, ay, bx, by), ac = cross2(ax, ay, cx, cy), bc = cross2(bx, by, cx, cy);
+  float c1 = -bc, c2 = ac, c3 = -ab;
+  const float c0 = -(c1 + c2 + c3);
+  const float S = fabsf(c0) + fabsf(c1) + fabsf(c2) + fabsf(c3);
+  if (!(S > 0.0f)) return false;
+  if (c0 < 0.0f) { c1 = -c1; c2 = -c2; c3 = -c3; }
+  const int t1 = c1 > 0.0f, t2 = c2 > 0.0f, t3 = c3 > 0.0f;
+  const int npos = t1 + t2 + t3;
+  const bool caseB = npos == 1;
+  const int p = t1 ? 1 : (t2 ? 2 : 3);
+  const int apex = npos == 0 ? 0 : (!t1 ? 1 : (!t2 ? 2 : 3));
+  const bool s12 = caseB && p == 2;
+  const bool s13 = (caseB && p == 3) || (!caseB && apex == 1);
+  const bool s23 = !caseB && apex == 2;
+  const bool s03 = !caseB && apex == 0;
+  int i0 = 0, i1 = 1, i2 = 2, i3 = 3;
+  cswap(s12, x1, x2); cswap(s12, y1, y2); cswap(s12, w1, w2); cswapi(s12, i1, i2);
+  cswap(s13, x1, x3); cswap(s13, y1, y3); cswap(s13, w1, w3); cswapi(s13, i1, i3);
+  cswap(s23, x2, x3); cswap(s23, y2, y3); cswap(s23, w2, w3); cswapi(s23, i2, i3);
+  cswap(s03, x0, x3); cswap(s03, y0, y3); cswap(s03, w0, w3); cswapi(s03, i0, i3);
+  k.x[0] = x0; k.x[1] = x1; k.x[2] = x2; k.x[3] = x3;
+  k.y[0] = y0; k.y[1] = y1; k.y[2] = y2; k.y[3] = y3;
+  k.w[0] = w0; k.w[1] = w1; k.w[2] = w2; k.w[3] = w3;
+  k.perm[0] = i0; k.perm[1] = i1; k.perm[2] = i2; k.perm[3] = i3;
+  k.caseB = caseB;
+  k.d1x = x1 - x0; k.d1y = y1 - y0;
+  k.d2x = x2 - x0; k.d2y = y2 - y0;
+  k.d3x = x3 - x0; k.d3y = y3 - y0;
+  k.D12 = cross2(k.d1x, k.d1y, k.d2x, k.d2y);
+  k.D13 = cross2(k.d1x, k.d1y, k.d3x, k.d3y);
+  k.D23 = cross2(k.d2x, k.d2y, k.d3x, k.d3y);
+  k.O123 = k.D12 + k.D23 - k.D13;
+  k.S = S;
+  return true;
+}
+
+// Hull edge of slot e in canonical indices: start j, edge vector, and the
+// orientations o1, o2 of the other two vertices against it.
+//   slot 0: (0,2) | 1,3    slot 1: (1,2) | 0,3
+//   slot 2: case B (1,3) | 0,2, case A (0,1) | 2,3
+//   slot 3: case B (0,3) | 1,2, case A unused
+struct EdgeRef {
+  int j, k, l1, l2;
+  float ex, ey, o1, o2;
+};
+
+__device__ __forceinline__ EdgeRef edge_ref(const TetCanon& K, int e) {
+  EdgeRef r;
+  if (e == 0) {
+    r.j = 0; r.k = 2; r.l1 = 1; r.l2 = 3; r.ex = K.d2x; r.ey = K.d2y; r.o1 = -K.D12; r.o2 = K.D23;
+  } else if (e == 1) {
+    r.j = 1; r.k = 2; r.l1 = 0; r.l2 = 3; r.ex = K.d2x - K.d1x; r.ey = K.d2y - K.d1y; r.o1 = K.D12; r.o2 = K.O123;
+  } else if (e == 2) {
+    if (K.caseB) {
+      r.j = 1; r.k = 3; r.l1 = 0; r.l2 = 2; r.ex = K.d3x - K.d1x; r.ey = K.d3y - K.d1y; r.o1 = K.D13; r.o2 = -K.O123;
+    } else {
+      r.j = 0; r.k = 1; r.l1 = 2; r.l2 = 3; r.ex = K.d1x; r.ey = K.d1y; r.o1 = K.D12; r.o2 = K.D13;
+    }
+  } else {
+    r.j = 0; r.k = 3; r.l1 = 1; r.l2 = 2; r.ex = K.d3x; r.ey = K.d3y; r.o1 = -K.D13; r.o2 = -K.D23;
+  }
+  return r;
+}
+
+__device__ __forceinline__ float sel4(const float* v, int i) {
+  return i == 0 ? v[0] : (i == 1 ? v[1] : (i == 2 ? v[2] : v[3]));
+}
+
+// Build the raster form of one tetrahedron from its four projected vertices
+// (relative pixel coordinates). Kn = 6 K (ortho) or 6 K / (Z0 Z1 Z2 Z3)
+// (perspective); wa = 1/Z of the anchor (perspective). Returns false for a
+// projection of zero area.
+template <bool PERSP>
+__device__ __forceinline__ bool tet_setup(float x0, float y0, float x1, float y1, float x2, float y2, float x3,
+                                          float y3, float w0, float w1, float w2, float w3, float Kn, float wa,
+                                          float invKn, TetRaster& t) {
+  t.xmin = fminf(fminf(x0, x1), fminf(x2, x3));
+  t.xmax = fmaxf(fmaxf(x0, x1), fmaxf(x2, x3));
+  t.ymin = fminf(fminf(y0, y1), fminf(y2, y3));
+  t.ymax = fmaxf(fmaxf(y0, y1), fmaxf(y2, y3));
+  TetCanon K;
+  if (!tet_canon(x0, y0, x1, y1, x2, y2, x3, y3, w0, w1, w2, w3, K)) return false;
+  const float tiny = K.S * K.S * 1e-12f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const EdgeRef r = edge_ref(K, e);
+    edge_fn(sel4(K.x, r.j), sel4(K.y, r.j), r.ex, r.ey, r.o1, r.o2, Kn, tiny, t.a[e], t.b[e], t.c[e]);
+  }
+  if (!K.caseB) {
+    t.a[3] = 0.0f;
+    t.b[3] = 0.0f;
+    t.c[3] = __int_as_float(0x7f800000);
+  }
+  if (PERSP) {
+    const float* X = K.x;
+    const float* Y = K.y;
+    const float* W = K.w;
+    const float C0 = fabsf(K.O123), C1 = fabsf(K.D23), C2 = fabsf(K.D13), C3 = fabsf(K.D12);
+    // Q > 0: the (0,1) diagonal (case B) / the outer face (case A) is the lower w surface
+    const float Q = K.caseB ? (C2 * W[2] + C3 * W[3]) - (C0 * W[0] + C1 * W[1])
+                            : C3 * W[3] - (C0 * W[0] + C1 * W[1] + C2 * W[2]);
+    bool ok1, ok2;
+    float pa0 = 0.f, pb0 = 0.f, pc0 = 0.f, pa1 = 0.f, pb1 = 0.f, pc1 = 0.f;
+    if (!K.caseB) {
+      ok1 = face_plane(X[0], Y[0], W[0], X[1], Y[1], W[1], X[2], Y[2], W[2], pa0, pb0, pc0);
+      ok2 = ok1;
+      pa1 = pa0; pb1 = pb0; pc1 = pc0;
+    } else {
+      const bool low01 = Q > 0.0f;
+      const int ip = low01 ? 0 : 2, iq = low01 ? 1 : 3, ir = low01 ? 2 : 0, is = low01 ? 3 : 1;
+      const float px = sel4(X, ip), py = sel4(Y, ip), pw = sel4(W, ip);
+      const float qx = sel4(X, iq), qy = sel4(Y, iq), qw = sel4(W, iq);
+      ok1 = face_plane(px, py, pw, qx, qy, qw, sel4(X, ir), sel4(Y, ir), sel4(W, ir), pa0, pb0, pc0);
+      ok2 = face_plane(px, py, pw, qx, qy, qw, sel4(X, is), sel4(Y, is), sel4(W, is), pa1, pb1, pc1);
+    }
+    if (!ok1 && !ok2) return false;
+    if (!ok1) { pa0 = pa1; pb0 = pb1; pc0 = pc1; }
+    if (!ok2) { pa1 = pa0; pb1 = pb0; pc1 = pc0; }
+    // sigma = -1 when the single outer face is the upper surface (case A)
+    const float sg = (!K.caseB && Q < 0.0f) ? -1.0f : 1.0f;
+    t.pa[0] = sg * pa0; t.pb[0] = sg * pb0; t.pc[0] = sg * (pc0 + wa);
+    t.pa[1] = sg * pa1; t.pb[1] = sg * pb1; t.pc[1] = sg * (pc1 + wa);
+    // the w-extent at the apex is 2|Q|/S and the pyramid apex value is 2 Kn / S
+    t.g = fabsf(Q) * invKn;
+  }
+  return true;
+}
+
+// Value of a set-up tetrahedron at relative pixel (X, Y) with row terms
+// e_row[e] = b[e] Y + c[e] (and p_row for perspective).
+template <bool PERSP>
+__device__ __forceinline__ float tet_value(const TetRaster& t, float X, const float* erow, const float* prow) {
+  float T = fminf(fminf(fmaf(t.a[0], X, erow[0]), fmaf(t.a[1], X, erow[1])),
+                  fminf(fmaf(t.a[2], X, erow[2]), fmaf(t.a[3], X, erow[3])));
+  T = fmaxf(T, 0.0f);
+  if (!PERSP) return T;
+  const float M = fmaxf(fmaf(t.pa[0], X, prow[0]), fmaf(t.pa[1], X, prow[1]));
+  const float den = M * fmaf(t.g, T, M);
+  return __fdividef(T, den);
+}
+
+// Pixel span [lo, hi] (relative X) of row terms where every edge function is
+// >= 0, widened by a small margin so that rounding never drops a pixel.
+__device__ __forceinline__ void row_span(const TetRaster& t, const float* erow, float& lo, float& hi) {
+  lo = -3.0e38f;
+  hi = 3.0e38f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float a = t.a[e];
+    const float xb = -erow[e] / a;
+    if (a > 0.0f) lo = fmaxf(lo, xb);
+    else if (a < 0.0f) hi = fminf(hi, xb);
+    else if (erow[e] < 0.0f) hi = -3.0e38f;
+  }
+  lo -= 1e-3f;
+  hi += 1e-3f;
+}
+
+// Split a non-negative accumulator-unit value into the two 32-bit shared
+// counters of a pixel (low 16 bits and the rest). Integer sums are exact and
+// associative, so the image does not depend on the order of fragments.
+__device__ __forceinline__ void accum_fixed(unsigned* lo, unsigned* hi, float q, unsigned* err) {
+  if (q < 4294967040.0f) {
+    const unsigned u = __float2uint_rn(q);
+    if (u) {
+      atomicAdd(lo, u & 0xFFFFu);
+      atomicAdd(hi, u >> 16);
+    }
+  } else {
+    const float qh = q * (1.0f / 65536.0f);
+    if (qh < 4294967040.0f) {
+      atomicAdd(hi, __float2uint_rn(qh));
+    } else {
+      atomicOr(err, kErrRange);
+    }
+  }
+}
+
+// Number of periodic copies: shift range s in [s0, s1] such that the span
+// [a + s P, b + s P] overlaps [lo, hi].
+__device__ __forceinline__ void shift_range(float a, float b, float lo, float hi, float P, bool wrap, int& s0,
+                                            int& s1) {
+  if (!wrap) { s0 = 0; s1 = 0; return; }
+  s0 = (int)ceilf((lo - b) / P);
+  s1 = (int)floorf((hi - a) / P);
+}
+
+}  // namespace lt

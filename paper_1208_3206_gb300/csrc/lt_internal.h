@@ -1,0 +1,56 @@
+// lt_internal.h -- host-side declarations shared by the library's .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lt_common.cuh"
+
+namespace lt {
+
+// ---- lt_build.cu: volumes, densities and position checks of every tetrahedron.
+cudaError_t launch_build_tets(const Lattice& L, int n_snap, double m, float* rho_out, DevCounters* ctr,
+                              cudaStream_t s);
+
+// ---- lt_bin.cu
+cudaError_t launch_bin_count(const Lattice& L, const FrameDev* d_frames, int n_frames, unsigned* d_count,
+                             DevCounters* ctr, cudaStream_t s);
+cudaError_t launch_scan(const unsigned* d_count, long long n, unsigned long long* d_off, unsigned long long* d_tmp,
+                        cudaStream_t s);
+size_t scan_tmp_words(long long n);
+cudaError_t launch_bin_scatter(const Lattice& L, const FrameDev* d_frames, int n_frames,
+                               const unsigned long long* d_off, unsigned* d_cursor, unsigned* d_list,
+                               unsigned long long capacity, DevCounters* ctr, cudaStream_t s);
+cudaError_t launch_worklist(const unsigned long long* d_off, long long n_tiles, unsigned* d_hist,
+                            unsigned long long* d_work, cudaStream_t s);
+
+// ---- lt_raster.cu
+struct RasterArgs {
+  Lattice L;
+  const FrameDev* frames;
+  const unsigned long long* off;
+  const unsigned* list;
+  const unsigned long long* work;
+  long long n_items;
+  float* image;
+  long long image_stride;  // floats per frame (W * H)
+  double* mass_tile;       // per global tile
+  DevCounters* ctr;
+  int tile;
+};
+cudaError_t launch_raster(const RasterArgs& a, int ctas, int threads, int any_persp, cudaStream_t s);
+int raster_max_ctas_per_sm(int threads, int tile, int any_persp);
+cudaError_t launch_count_fragments(const RasterArgs& a, unsigned long long* d_counts, int n_frames, int ctas,
+                                   int threads, cudaStream_t s);
+cudaError_t launch_mass_reduce(const double* mass_tile, long long tpf, int n_frames, double* d_mass,
+                               cudaStream_t s);
+cudaError_t launch_atomic(const Lattice& L, const FrameDev* d_frames, long long stride, int n_frames, float* image,
+                          DevCounters* ctr, cudaStream_t s);
+
+// ---- lt_backward.cu
+cudaError_t launch_backward(const Lattice& L, const FrameDev* d_frames, long long stride, int n_frames, int n_snap,
+                            const float* dLdI, float* corner_grad, cudaStream_t s);
+cudaError_t launch_gather_grad(const Lattice& L, int n_snap, const float* corner_grad, float* dLdpos,
+                               cudaStream_t s);
+
+}  // namespace lt

@@ -1,0 +1,285 @@
+// lt_raster.cu -- the projection of Eq. 6 over binned tiles (persistent,
+// fixed-point on-chip accumulation), the plain one-cube-per-thread atomic
+// form, the fragment counter and the per-frame mass reduction.
+#include "lt_internal.h"
+
+namespace lt {
+
+// Visit every (tetrahedron, pixel) fragment candidate of one cube inside the
+// pixel rectangle [px0, px1] x [py0, py1] (absolute, inclusive), for every
+// periodic copy of the cube that reaches it. fn(px, py, value) is called for
+// candidates with value > 0 (value in accumulator units, before the
+// perspective ray-length factor).
+template <bool PERSP, typename Fn>
+__device__ __forceinline__ void cube_fragments(const CubeProj& P, const FrameDev& F, int px0, int px1, int py0,
+                                               int py1, Fn&& fn) {
+  int sx0, sx1, sy0, sy1;
+  const bool wrap = (!PERSP) && F.wrap;
+  const float axa = P.axh + P.axl, aya = P.ayh + P.ayl;  // approximate anchor, for ranges only
+  shift_range(axa + P.xmin, axa + P.xmax, (float)px0 - 0.5f, (float)px1 + 0.5f, (float)F.W, wrap, sx0, sx1);
+  shift_range(aya + P.ymin, aya + P.ymax, (float)py0 - 0.5f, (float)py1 + 0.5f, (float)F.H, wrap, sy0, sy1);
+  // a cube cannot span more than a few periods of a periodic window when its
+  // particles moved less than half a box; cap the copies of invalid input
+  sx1 = min(sx1, sx0 + 63);
+  sy1 = min(sy1, sy0 + 63);
+  for (int sy = sy0; sy <= sy1; ++sy) {
+    for (int sx = sx0; sx <= sx1; ++sx) {
+      const int shx = sx * F.W, shy = sy * F.H;
+      const float ax = axa + (float)shx, ay = aya + (float)shy;
+#pragma unroll
+      for (int s = 0; s < 6; ++s) {
+        const int c0 = tet_corner(s, 0), c1 = tet_corner(s, 1), c2 = tet_corner(s, 2), c3 = tet_corner(s, 3);
+        const float txmin = fminf(fminf(P.x[c0], P.x[c1]), fminf(P.x[c2], P.x[c3]));
+        const float txmax = fmaxf(fmaxf(P.x[c0], P.x[c1]), fmaxf(P.x[c2], P.x[c3]));
+        const float tymin = fminf(fminf(P.y[c0], P.y[c1]), fminf(P.y[c2], P.y[c3]));
+        const float tymax = fmaxf(fmaxf(P.y[c0], P.y[c1]), fmaxf(P.y[c2], P.y[c3]));
+        const int qx0 = max(px0, (int)ceilf(ax + txmin - 1e-3f)), qx1 = min(px1, (int)floorf(ax + txmax + 1e-3f));
+        const int qy0 = max(py0, (int)ceilf(ay + tymin - 1e-3f)), qy1 = min(py1, (int)floorf(ay + tymax + 1e-3f));
+        if (qx0 > qx1 || qy0 > qy1) continue;
+        float Kn = 6.0f * F.K, invKn = 0.0f;
+        if (PERSP) {
+          const float zz = P.z[c0] * P.z[c1] * P.z[c2] * P.z[c3];
+          Kn = Kn / zz;
+          invKn = 1.0f / Kn;
+        }
+        TetRaster t;
+        if (!tet_setup<PERSP>(P.x[c0], P.y[c0], P.x[c1], P.y[c1], P.x[c2], P.y[c2], P.x[c3], P.y[c3],
+                              PERSP ? P.dw[c0] : 0.f, PERSP ? P.dw[c1] : 0.f, PERSP ? P.dw[c2] : 0.f,
+                              PERSP ? P.dw[c3] : 0.f, Kn, P.w0, invKn, t))
+          continue;
+        for (int py = qy0; py <= qy1; ++py) {
+          const float Y = rel_coord(py, shy, P.ayh, P.ayl);
+          float erow[4], prow[2];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) erow[e] = fmaf(t.b[e], Y, t.c[e]);
+          if (PERSP) {
+            prow[0] = fmaf(t.pb[0], Y, t.pc[0]);
+            prow[1] = fmaf(t.pb[1], Y, t.pc[1]);
+          }
+          float lo, hi;
+          row_span(t, erow, lo, hi);
+          const int xa = max(qx0, (int)ceilf(fmaxf(lo + ax, -1.0e9f)));
+          const int xb = min(qx1, (int)floorf(fminf(hi + ax, 1.0e9f)));
+          for (int px = xa; px <= xb; ++px) {
+            const float v = tet_value<PERSP>(t, rel_coord(px, shx, P.axh, P.axl), erow, prow);
+            if (v > 0.0f) fn(px, py, v);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Perspective ray-direction length |d| = sqrt(1 + x^2 + y^2) of pixel (px, py).
+__device__ __forceinline__ float ray_len(const FrameDev& F, int px, int py) {
+  const float xt = F.tan_x * (2.0f * ((float)px + 0.5f) / (float)F.W - 1.0f);
+  const float yt = F.tan_y * (2.0f * ((float)py + 0.5f) / (float)F.H - 1.0f);
+  return sqrtf(1.0f + xt * xt + yt * yt);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent tile raster.
+
+template <bool ANY_PERSP>
+__global__ void k_raster(RasterArgs a) {
+  extern __shared__ unsigned smem[];
+  const int T = a.tile;
+  unsigned* acc_lo = smem;
+  unsigned* acc_hi = smem + T * T;
+  __shared__ unsigned long long item_s;
+  __shared__ double mass_w[32];
+  const int nthr = blockDim.x;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(&a.ctr->work_next, 1ull);
+    for (int i = threadIdx.x; i < 2 * T * T; i += nthr) smem[i] = 0u;
+    __syncthreads();
+    const unsigned long long item = item_s;
+    if (item >= (unsigned long long)a.n_items) break;
+    const long long tg = (long long)a.work[item];
+    const FrameDev* Fp = a.frames;
+    // frame of this tile: frames share one tile grid
+    const long long tpf = (long long)Fp[0].tiles_x * Fp[0].tiles_y;
+    const int f = (int)(tg / tpf);
+    const FrameDev& F = Fp[f];
+    const long long tl = tg - (long long)f * tpf;
+    const int tyi = (int)(tl / F.tiles_x), txi = (int)(tl - (long long)tyi * F.tiles_x);
+    const int px0 = txi * T, py0 = tyi * T;
+    const int px1 = min(px0 + T, F.W) - 1, py1 = min(py0 + T, F.H) - 1;
+    const unsigned long long e0 = a.off[tg], e1 = a.off[tg + 1];
+    bool dummy = true;
+    for (unsigned long long e = e0 + threadIdx.x; e < e1; e += nthr) {
+      const long long cube = (long long)a.list[e];
+      CubeProj P;
+      auto acc = [&](int px, int py, float v) {
+        const int li = (py - py0) * T + (px - px0);
+        accum_fixed(&acc_lo[li], &acc_hi[li], v, &a.ctr->errors);
+      };
+      if (ANY_PERSP && F.persp) {
+        if (!project_cube<true>(a.L, F, cube, P, dummy)) continue;
+        cube_fragments<true>(P, F, px0, px1, py0, py1, acc);
+      } else {
+        if (!project_cube<false>(a.L, F, cube, P, dummy)) continue;
+        cube_fragments<false>(P, F, px0, px1, py0, py1, acc);
+      }
+    }
+    __syncthreads();
+    // one store per pixel, and the tile's share of the frame mass
+    double msum = 0.0;
+    const int tw = px1 - px0 + 1, th = py1 - py0 + 1;
+    float* img = a.image + (long long)f * a.image_stride;
+    for (int li = threadIdx.x; li < tw * th; li += nthr) {
+      const int ly = li / tw, lx = li - ly * tw;
+      const int si = ly * T + lx;
+      const unsigned long long q = ((unsigned long long)acc_hi[si] << 16) + (unsigned long long)acc_lo[si];
+      double v = (double)q * F.unit;
+      if (ANY_PERSP && F.persp) v *= (double)ray_len(F, px0 + lx, py0 + ly);
+      const float vf = (float)v;
+      img[(long long)(py0 + ly) * F.W + (px0 + lx)] = vf;
+      msum += (double)vf;
+    }
+    // fixed-shape reduction: warp shuffles, then warp 0 over the warp sums
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) msum += __shfl_down_sync(0xffffffffu, msum, o);
+    if ((threadIdx.x & 31) == 0) mass_w[threadIdx.x >> 5] = msum;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double w = threadIdx.x < (unsigned)(nthr >> 5) ? mass_w[threadIdx.x] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+      if (threadIdx.x == 0) a.mass_tile[tg] = w * F.pix_area;
+    }
+    __syncthreads();
+  }
+}
+
+int raster_max_ctas_per_sm(int threads, int tile, int any_persp) {
+  int n = 0;
+  const size_t smem = sizeof(unsigned) * 2 * tile * tile;
+  if (any_persp)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster<true>, threads, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster<false>, threads, smem);
+  return n < 1 ? 1 : n;
+}
+
+cudaError_t launch_raster(const RasterArgs& a, int ctas, int threads, int any_persp, cudaStream_t s) {
+  const size_t smem = sizeof(unsigned) * 2 * a.tile * a.tile;
+  if (any_persp) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_raster<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_raster<true><<<ctas, threads, smem, s>>>(a);
+  } else {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_raster<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_raster<false><<<ctas, threads, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fragment counter over the same bins (chord > 0 pairs).
+
+__global__ void k_count(RasterArgs a, unsigned long long* __restrict__ counts) {
+  __shared__ unsigned long long item_s;
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(&a.ctr->work_next, 1ull);
+    __syncthreads();
+    const unsigned long long item = item_s;
+    __syncthreads();
+    if (item >= (unsigned long long)a.n_items) break;
+    const long long tg = (long long)a.work[item];
+    const long long tpf = (long long)a.frames[0].tiles_x * a.frames[0].tiles_y;
+    const int f = (int)(tg / tpf);
+    const FrameDev& F = a.frames[f];
+    const long long tl = tg - (long long)f * tpf;
+    const int tyi = (int)(tl / F.tiles_x), txi = (int)(tl - (long long)tyi * F.tiles_x);
+    const int T = a.tile;
+    const int px0 = txi * T, py0 = tyi * T;
+    const int px1 = min(px0 + T, F.W) - 1, py1 = min(py0 + T, F.H) - 1;
+    unsigned long long n = 0;
+    bool dummy = true;
+    for (unsigned long long e = a.off[tg] + threadIdx.x; e < a.off[tg + 1]; e += blockDim.x) {
+      const long long cube = (long long)a.list[e];
+      CubeProj P;
+      auto cnt = [&](int, int, float) { ++n; };
+      if (F.persp) {
+        if (!project_cube<true>(a.L, F, cube, P, dummy)) continue;
+        cube_fragments<true>(P, F, px0, px1, py0, py1, cnt);
+      } else {
+        if (!project_cube<false>(a.L, F, cube, P, dummy)) continue;
+        cube_fragments<false>(P, F, px0, px1, py0, py1, cnt);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(&counts[f], n);
+  }
+}
+
+cudaError_t launch_count_fragments(const RasterArgs& a, unsigned long long* d_counts, int n_frames, int ctas,
+                                   int threads, cudaStream_t s) {
+  (void)n_frames;
+  k_count<<<ctas, threads, 0, s>>>(a, d_counts);
+  return cudaGetLastError();
+}
+
+// Per-frame mass: fixed-order sum of the frame's tile partials.
+__global__ void k_mass_reduce(const double* __restrict__ mass_tile, long long tpf, double* __restrict__ d_mass) {
+  __shared__ double ws[32];
+  const int f = blockIdx.x;
+  double s = 0.0;
+  for (long long t = threadIdx.x; t < tpf; t += blockDim.x) s += mass_tile[(long long)f * tpf + t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) d_mass[f] = w;
+  }
+}
+
+cudaError_t launch_mass_reduce(const double* mass_tile, long long tpf, int n_frames, double* d_mass,
+                               cudaStream_t s) {
+  k_mass_reduce<<<n_frames, 256, 0, s>>>(mass_tile, tpf, d_mass);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Plain form: one thread per (frame, cube), float atomics into the image.
+
+template <bool PERSP>
+__device__ __forceinline__ void atomic_cube(const Lattice& L, const FrameDev& F, long long cube, float* img,
+                                            DevCounters* ctr) {
+  CubeProj P;
+  bool ok = true;
+  if (!project_cube<PERSP>(L, F, cube, P, ok)) return;
+  const double unit = F.unit;
+  cube_fragments<PERSP>(P, F, 0, F.W - 1, 0, F.H - 1, [&](int px, int py, float v) {
+    float val = (float)((double)v * unit);
+    if (PERSP) val *= ray_len(F, px, py);
+    atomicAdd(&img[(long long)py * F.W + px], val);
+  });
+}
+
+__global__ void __launch_bounds__(256) k_atomic(Lattice L, const FrameDev* __restrict__ frames, long long stride,
+                                                float* __restrict__ image, DevCounters* ctr) {
+  const FrameDev& F = frames[blockIdx.y];
+  float* img = image + (long long)blockIdx.y * stride;
+  for (long long cube = (long long)blockIdx.x * blockDim.x + threadIdx.x; cube < L.n_particles;
+       cube += (long long)gridDim.x * blockDim.x) {
+    if (F.persp) atomic_cube<true>(L, F, cube, img, ctr);
+    else atomic_cube<false>(L, F, cube, img, ctr);
+  }
+}
+
+cudaError_t launch_atomic(const Lattice& L, const FrameDev* d_frames, long long stride, int n_frames, float* image,
+                          DevCounters* ctr, cudaStream_t s) {
+  long long b = (L.n_particles + 255) / 256;
+  if (b > 4096) b = 4096;
+  dim3 grid((unsigned)(b < 1 ? 1 : b), n_frames);
+  k_atomic<<<grid, 256, 0, s>>>(L, d_frames, stride, image, ctr);
+  return cudaGetLastError();
+}
+
+}  // namespace lt

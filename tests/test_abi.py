@@ -1,0 +1,56 @@
+"""The C ABI library loads and exports every entry point declared in
+include/lt.h (no GPU needed, no compute calls)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:lt_status|void|const char\*)\s+(lt_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1208_3206_gb300 import _build, _lib
+    _build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lt_build_tets", "lt_project_bin", "lt_render_tiles", "lt_render_backward"):
+        assert required in names
+    assert len(names) >= 16
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1208_3206_gb300 import _lib
+    names = declared_functions()
+    assert sorted(_lib.EXPORTS) == names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_and_null_arguments(lib):
+    for code in range(9):
+        assert lib.lt_status_str(code)
+    assert lib.lt_status_str(99) == b"unknown status"
+    # argument checks happen before any CUDA call
+    assert lib.lt_create(None, None) == 1
+    assert lib.lt_build_tets(None, None, 0, 4, 1.0, 1.0, 1, None, None) == 1
+    assert lib.lt_project_bin(None, None, 1, None, None) == 1
+    assert lib.lt_render_tiles(None, None, None, None) == 1
+    assert lib.lt_render_backward(None, None, None, None) == 1
+    assert lib.lt_sync(None, None) == 1
+
+
+def test_library_is_sm103a_only():
+    from paper_1208_3206_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
