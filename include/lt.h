@@ -108,6 +108,8 @@ typedef struct {
   long long nonfinite;       /* non-finite positions seen */
   long long behind_eye;      /* cubes skipped because a vertex is behind the eye */
   long long range_overflow;  /* pixels that left the accumulator range */
+  long long exact_fragments; /* ill-conditioned fragments re-evaluated in FP64 (cumulative) */
+  long long queue_overflow;  /* such fragments left in FP32 because a tile's queue was full */
   int n_frames;              /* frames of the last lt_project_bin */
   int tile;                  /* tile edge in use */
   int graph_kernels;         /* kernel nodes in the graph of the last lt_graph_build */

@@ -45,6 +45,8 @@ class LtStats(C.Structure):
         ("nonfinite", C.c_longlong),
         ("behind_eye", C.c_longlong),
         ("range_overflow", C.c_longlong),
+        ("exact_fragments", C.c_longlong),
+        ("queue_overflow", C.c_longlong),
         ("n_frames", C.c_int),
         ("tile", C.c_int),
         ("graph_kernels", C.c_int),

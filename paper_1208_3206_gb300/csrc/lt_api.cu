@@ -231,6 +231,8 @@ bool make_frame(const lt_camera& c, const lt_ctx* ctx, int snapshot, int tile, i
     const double tx = ty * c.W / c.H;
     F.tan_x = (float)tx;
     F.tan_y = (float)ty;
+    F.tand[0] = tx;
+    F.tand[1] = ty;
     F.kx = (float)(c.W / (2.0 * tx));
     F.ky = (float)(c.H / (2.0 * ty));
     split_ff(c.W / (2.0 * tx), &F.kxh, &F.kxl);
@@ -252,6 +254,20 @@ bool make_frame(const lt_camera& c, const lt_ctx* ctx, int snapshot, int tile, i
     F.pix_area = (2.0 * tx / c.W) * (2.0 * ty / c.H);
   }
   F.inv6K = (float)(1.0 / (6.0 * (double)F.K));
+  for (int q = 0; q < 3; ++q) {
+    F.rd[q] = r[q];
+    F.ud[q] = u[q];
+    F.fd[q] = f[q];
+    F.eyed[q] = c.eye[q];
+  }
+  if (!F.persp) {
+    F.lod[0] = c.lo[0];
+    F.lod[1] = c.lo[1];
+    F.pxd[0] = ((double)c.hi[0] - c.lo[0]) / c.W;
+    F.pxd[1] = ((double)c.hi[1] - c.lo[1]) / c.H;
+  }
+  F.m_tet = m;
+  F.sigma_units = (float)scale_bits;
   return true;
 }
 
@@ -377,7 +393,9 @@ lt_status render_impl(lt_ctx* ctx, float* d_image, double* d_mass, cudaStream_t 
   a.tile = ctx->tile;
   const int threads = ctx->cfg.raster_threads;
   int cps = ctx->cfg.ctas_per_sm;
-  if (cps <= 0) cps = lt::raster_max_ctas_per_sm(threads, ctx->tile, ctx->any_persp);
+  const int fit = lt::raster_max_ctas_per_sm(threads, ctx->tile, ctx->any_persp);
+  if (fit < 1) return LT_ERR_ARG;  // CTA shape exceeds the SM's registers or shared memory
+  if (cps <= 0 || cps > fit) cps = fit;
   long long ctas = (long long)ctx->num_sms * cps;
   if (ctas > ctx->n_tiles) ctas = ctx->n_tiles;
   if (ctas < 1) ctas = 1;
@@ -646,6 +664,7 @@ lt_status lt_autotune(lt_ctx* ctx, const lt_camera* cams, int n_frames, const in
       c.tile = ti;
       c.raster_threads = th;
       c.ctas_per_sm = 0;
+      if (lt::raster_max_ctas_per_sm(th, ti, 1) < 1 || lt::raster_max_ctas_per_sm(th, ti, 0) < 1) continue;
       ctx->cfg = c;
       lt_status st = project_bin_impl(ctx, cams, n_frames, frame_snapshot, s, false);
       if (st == LT_OK) st = render_impl(ctx, d_image, nullptr, s);
@@ -695,6 +714,8 @@ lt_status lt_get_stats(lt_ctx* ctx, lt_stats* out) {
   out->nonfinite = (long long)c.nonfinite;
   out->behind_eye = (long long)c.behind_eye;
   out->range_overflow = (long long)c.range_overflow;
+  out->exact_fragments = (long long)c.exact_fragments;
+  out->queue_overflow = (long long)c.queue_overflow;
   out->n_frames = ctx->n_frames;
   out->tile = ctx->tile;
   out->graph_kernels = ctx->graph_kernels;

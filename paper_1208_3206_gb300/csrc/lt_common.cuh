@@ -65,6 +65,8 @@ struct DevCounters {
   unsigned long long range_overflow;
   unsigned long long work_next;   // persistent raster work counter
   unsigned long long total_entries;
+  unsigned long long exact_fragments;  // fragments re-evaluated in FP64
+  unsigned long long queue_overflow;   // ill-conditioned fragments kept in FP32 (queue full)
 };
 
 // Snapshot description.
@@ -98,6 +100,13 @@ struct FrameDev {
   float tan_x, tan_y;     // perspective image-plane half extents at unit distance
   double unit;            // accumulator unit -> column density
   double pix_area;        // pixel area for the frame mass
+  // double-precision view for the exact evaluation of ill-conditioned fragments
+  double rd[3], ud[3], fd[3], eyed[3];
+  double lod[2], pxd[2];  // ortho window origin and pixel size (world units)
+  double tand[2];         // perspective tan(fov/2) in x and y
+  double m_tet;           // mass of one tetrahedron
+  float sigma_units;      // mean column density in accumulator units (2^frac_bits)
+  float pad_;
 };
 
 // ---------------------------------------------------------------------------
@@ -263,6 +272,81 @@ __device__ __forceinline__ bool project_cube(const Lattice& L, const FrameDev& F
   return true;
 }
 
+// Corner n (0..7) of column c of row s of the connectivity table, for a
+// run-time row index (rows 0..4 packed 12 bits each, row 5 separately).
+__device__ __forceinline__ int tet_corner_dyn(int s, int c) {
+  constexpr unsigned long long P =
+      (unsigned long long)tet_corner(0, 0) | ((unsigned long long)tet_corner(0, 1) << 3) |
+      ((unsigned long long)tet_corner(0, 2) << 6) | ((unsigned long long)tet_corner(0, 3) << 9) |
+      ((unsigned long long)tet_corner(1, 0) << 12) | ((unsigned long long)tet_corner(1, 1) << 15) |
+      ((unsigned long long)tet_corner(1, 2) << 18) | ((unsigned long long)tet_corner(1, 3) << 21) |
+      ((unsigned long long)tet_corner(2, 0) << 24) | ((unsigned long long)tet_corner(2, 1) << 27) |
+      ((unsigned long long)tet_corner(2, 2) << 30) | ((unsigned long long)tet_corner(2, 3) << 33) |
+      ((unsigned long long)tet_corner(3, 0) << 36) | ((unsigned long long)tet_corner(3, 1) << 39) |
+      ((unsigned long long)tet_corner(3, 2) << 42) | ((unsigned long long)tet_corner(3, 3) << 45) |
+      ((unsigned long long)tet_corner(4, 0) << 48) | ((unsigned long long)tet_corner(4, 1) << 51) |
+      ((unsigned long long)tet_corner(4, 2) << 54) | ((unsigned long long)tet_corner(4, 3) << 57);
+  constexpr unsigned R5 = (unsigned)tet_corner(5, 0) | ((unsigned)tet_corner(5, 1) << 3) |
+                          ((unsigned)tet_corner(5, 2) << 6) | ((unsigned)tet_corner(5, 3) << 9);
+  return s < 5 ? (int)((P >> (12 * s + 3 * c)) & 7ull) : (int)((R5 >> (3 * c)) & 7u);
+}
+
+// The four vertices of tetrahedron s of a cube, projected like project_cube.
+struct TetProj {
+  float x[4], y[4], dw[4], z[4];
+  float axh, axl, ayh, ayl, w0;
+};
+
+// Returns false for non-finite input or a tetrahedron not entirely in front
+// of a perspective eye (those cubes are counted by the bin pass).
+template <bool PERSP>
+__device__ __forceinline__ bool project_tet(const Lattice& L, const FrameDev& F, long long cube, int s, TetProj& P) {
+  const int N = L.N;
+  const int i = (int)(cube % N);
+  const int j = (int)((cube / N) % N);
+  const int k = (int)(cube / ((long long)N * N));
+  const long long snap_off = (long long)F.snapshot * L.n_particles;
+  bool ok = true;
+  if (!PERSP) {
+    anchor_affine(F, 0, i, j, k, P.axh, P.axl);
+    anchor_affine(F, 1, i, j, k, P.ayh, P.ayl);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float3 l = load_corner(L, snap_off, i, j, k, tet_corner_dyn(s, c), ok);
+      P.x[c] = (F.r[0] * l.x + F.r[1] * l.y + F.r[2] * l.z) * F.sx;
+      P.y[c] = (F.u[0] * l.x + F.u[1] * l.y + F.u[2] * l.z) * F.sy;
+      P.dw[c] = 0.f;
+      P.z[c] = 1.f;
+    }
+    P.w0 = 0.f;
+    return ok;
+  }
+  float Xh, Xl, Yh, Yl, Zh, Zl;
+  anchor_affine(F, 0, i, j, k, Xh, Xl);
+  anchor_affine(F, 1, i, j, k, Yh, Yl);
+  anchor_affine(F, 2, i, j, k, Zh, Zl);
+  const float X0 = Xh + Xl, Y0 = Yh + Yl, Z0 = Zh + Zl;
+  bool front = Z0 > F.near_z;
+  ff_project(Xh, Xl, Zh, Zl, F.kxh, F.kxl, F.cx, P.axh, P.axl);
+  ff_project(Yh, Yl, Zh, Zl, F.kyh, F.kyl, F.cy, P.ayh, P.ayl);
+  P.w0 = 1.0f / Z0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float3 l = load_corner(L, snap_off, i, j, k, tet_corner_dyn(s, c), ok);
+    const float dX = F.r[0] * l.x + F.r[1] * l.y + F.r[2] * l.z;
+    const float dY = F.u[0] * l.x + F.u[1] * l.y + F.u[2] * l.z;
+    const float dZ = F.f[0] * l.x + F.f[1] * l.y + F.f[2] * l.z;
+    const float Zn = Z0 + dZ;
+    front = front && (Zn > F.near_z);
+    const float inv = 1.0f / (Zn * Z0);
+    P.x[c] = (dX * Z0 - X0 * dZ) * inv * F.kx;
+    P.y[c] = (dY * Z0 - Y0 * dZ) * inv * F.ky;
+    P.dw[c] = -dZ * inv;
+    P.z[c] = Zn;
+  }
+  return ok && front;
+}
+
 // ---------------------------------------------------------------------------
 // Per-tetrahedron setup.
 
@@ -274,6 +358,10 @@ struct TetRaster {
   float pa[2], pb[2], pc[2];
   float g;
   float xmin, xmax, ymin, ymax;  // relative bounding box
+  // steepness |e|^2 / min(|o1|, |o2|) of each edge (0 for unused slots): the
+  // FP32 round-off of an edge's value grows in proportion to it
+  float st[4];
+  float hmax;  // upper bound of the value over the tetrahedron (accumulator units)
 };
 
 __device__ __forceinline__ float cross2(float ax, float ay, float bx, float by) { return ax * by - ay * bx; }
@@ -307,7 +395,8 @@ __device__ __forceinline__ bool face_plane(float xp, float yp, float wp, float x
   const float nw = ux * vy - uy * vx;
   const float nx = uy * vw - uw * vy;
   const float ny = uw * vx - ux * vw;
-  if (nw == 0.0f) return false;
+  // a face seen nearly edge-on has an unreliable FP32 slope: treat as vertical
+  if (!(fabsf(nw) > 1e-5f * (fabsf(ux * vy) + fabsf(uy * vx)))) return false;
   const float inw = 1.0f / nw;
   pa = -nx * inw;
   pb = -ny * inw;
@@ -426,11 +515,20 @@ __device__ __forceinline__ bool tet_setup(float x0, float y0, float x1, float y1
   for (int e = 0; e < 4; ++e) {
     const EdgeRef r = edge_ref(K, e);
     edge_fn(sel4(K.x, r.j), sel4(K.y, r.j), r.ex, r.ey, r.o1, r.o2, Kn, tiny, t.a[e], t.b[e], t.c[e]);
+    const float omin = fminf(fabsf(r.o1), fabsf(r.o2));
+    t.st[e] = (r.ex * r.ex + r.ey * r.ey) / fmaxf(omin, tiny);
   }
   if (!K.caseB) {
     t.a[3] = 0.0f;
     t.b[3] = 0.0f;
     t.c[3] = __int_as_float(0x7f800000);
+    t.st[3] = 0.0f;
+  }
+  // pyramid apex value 2 Kn / S; the perspective depth factor is at most 1 / w_min^2
+  t.hmax = 2.0f * Kn / K.S;
+  if (PERSP) {
+    const float wmin = wa + fminf(fminf(w0, w1), fminf(w2, w3));
+    t.hmax = t.hmax / (wmin * wmin);
   }
   if (PERSP) {
     const float* X = K.x;
@@ -515,6 +613,118 @@ __device__ __forceinline__ void accum_fixed(unsigned* lo, unsigned* hi, float q,
       atomicOr(err, kErrRange);
     }
   }
+}
+
+// Exact value of rho_t * dl_t (Eq. 3, 6, 9) for tetrahedron s of `cube` at
+// pixel (px, py) of the copy shifted by (sx, sy) periods, in FP64 from the
+// stored positions: the ray through the pixel centre clipped against the four
+// face planes. Used for the rare fragments whose FP32 evaluation is
+// ill-conditioned. Returns the value in column-density units divided by the
+// pixel's ray-direction length for perspective frames (the factor the tile
+// applies when it stores the pixel).
+__device__ __noinline__ static double exact_fragment(const Lattice& L, const FrameDev& F, long long cube, int s, int sx, int sy, int px,
+                                 int py, double m) {
+  const int N = L.N;
+  const int i = (int)(cube % N), j = (int)((cube / N) % N), k = (int)(cube / ((long long)N * N));
+  const long long soff = (long long)F.snapshot * L.n_particles;
+  const double h = (double)L.box / N, box = (double)L.box;
+  double v[4][3];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int n = tet_corner_dyn(s, c);
+    const int a = n & 1, b = (n >> 1) & 1, cc = (n >> 2) & 1;
+    const int ii = i + a, jj = j + b, kk = k + cc;
+    const int im = ii == N ? 0 : ii, jm = jj == N ? 0 : jj, km = kk == N ? 0 : kk;
+    const long long id = soff + particle_id(im, jm, km, N);
+    double d[3];
+    if (L.fmt == 0) {
+      const float4 p = __ldg(reinterpret_cast<const float4*>(L.pos) + id);
+      const double pp[3] = {p.x, p.y, p.z};
+      const int ix[3] = {im, jm, km};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        double dd = pp[q] - ix[q] * h;
+        if (dd > 0.5 * box) dd -= box;
+        else if (dd < -0.5 * box) dd += box;
+        d[q] = dd;
+      }
+    } else {
+      bool ok = true;
+      const float3 df = load_disp(L, soff, i, j, k, n, ok);
+      d[0] = df.x; d[1] = df.y; d[2] = df.z;
+    }
+    v[c][0] = (i + a) * h + d[0];
+    v[c][1] = (j + b) * h + d[1];
+    v[c][2] = (k + cc) * h + d[2];
+  }
+  // signed volume (Eq. 9) and density (Eq. 3)
+  double e1[3], e2[3], e3[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    e1[q] = v[1][q] - v[0][q];
+    e2[q] = v[2][q] - v[0][q];
+    e3[q] = v[3][q] - v[0][q];
+  }
+  const double V = (e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) + e1[1] * (e2[2] * e3[0] - e2[0] * e3[2]) +
+                    e1[2] * (e2[0] * e3[1] - e2[1] * e3[0])) / 6.0;
+  if (V == 0.0) return 0.0;
+  // pixel ray
+  double o[3], dir[3];
+  bool half = F.persp != 0;
+  if (!half) {
+    const double a = F.lod[0] + ((double)px - (double)sx * F.W + 0.5) * F.pxd[0];
+    const double b = F.lod[1] + ((double)py - (double)sy * F.H + 0.5) * F.pxd[1];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      o[q] = a * F.rd[q] + b * F.ud[q];
+      dir[q] = F.fd[q];
+    }
+  } else {
+    const double xt = F.tand[0] * (2.0 * ((double)px + 0.5) / F.W - 1.0);
+    const double yt = F.tand[1] * (2.0 * ((double)py + 0.5) / F.H - 1.0);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      o[q] = F.eyed[q];
+      dir[q] = F.fd[q] + xt * F.rd[q] + yt * F.ud[q];
+    }
+  }
+  const double dl = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  // clip t (point o + t dir) against the four outward half-spaces
+  double t_in = half ? 0.0 : -1e300, t_out = 1e300;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const double* A = v[(f + 1) & 3];
+    const double* B = v[(f + 2) & 3];
+    const double* C = v[(f + 3) & 3];
+    const double u1[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+    const double u2[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+    double nn[3] = {u1[1] * u2[2] - u1[2] * u2[1], u1[2] * u2[0] - u1[0] * u2[2], u1[0] * u2[1] - u1[1] * u2[0]};
+    const double side = nn[0] * (v[f][0] - A[0]) + nn[1] * (v[f][1] - A[1]) + nn[2] * (v[f][2] - A[2]);
+    if (side > 0.0) { nn[0] = -nn[0]; nn[1] = -nn[1]; nn[2] = -nn[2]; }
+    const double den = nn[0] * dir[0] + nn[1] * dir[1] + nn[2] * dir[2];
+    const double num = nn[0] * (A[0] - o[0]) + nn[1] * (A[1] - o[1]) + nn[2] * (A[2] - o[2]);
+    if (den > 0.0) t_out = fmin(t_out, num / den);
+    else if (den < 0.0) t_in = fmax(t_in, num / den);
+    else if (num < 0.0) return 0.0;
+  }
+  if (!(t_out > t_in)) return 0.0;
+  const double chord = (t_out - t_in) * dl;
+  const double val = m / fabs(V) * chord;
+  return half ? val / dl : val;
+}
+
+// A fragment's FP32 value carries a relative error of about kFragErr times
+// the steepness of its active pyramid edge; it is recomputed exactly when
+// that error could exceed kFragTol of max(value, mean column density).
+constexpr float kFragErr = 1e-5f;
+constexpr float kFragTol = 1e-5f;
+
+// True when some fragment of a set-up tetrahedron may need the exact path:
+// its steepest edge's round-off bound could pass kFragTol of
+// max(value, mean column density) somewhere.
+__device__ __forceinline__ bool may_need_exact(const TetRaster& t, float sigma_units) {
+  const float stmax = fmaxf(fmaxf(t.st[0], t.st[1]), fmaxf(t.st[2], t.st[3]));
+  return stmax * kFragErr * t.hmax > kFragTol * fminf(t.hmax, sigma_units);
 }
 
 // Number of periodic copies: shift range s in [s0, s1] such that the span

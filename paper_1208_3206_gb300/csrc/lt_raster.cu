@@ -1,6 +1,5 @@
-// lt_raster.cu -- the projection of Eq. 6 over binned tiles (persistent,
-// fixed-point on-chip accumulation), the plain one-cube-per-thread atomic
-// form, the fragment counter and the per-frame mass reduction.
+// lt_raster.cu -- the plain one-cube-per-thread atomic form of Eq. 6 and the
+// per-frame mass reduction (the tiled raster is in lt_tile.cu).
 #include "lt_internal.h"
 
 namespace lt {
@@ -10,9 +9,9 @@ namespace lt {
 // periodic copy of the cube that reaches it. fn(px, py, value) is called for
 // candidates with value > 0 (value in accumulator units, before the
 // perspective ray-length factor).
-template <bool PERSP, typename Fn>
+template <bool PERSP, bool EXACT, typename Fn>
 __device__ __forceinline__ void cube_fragments(const CubeProj& P, const FrameDev& F, int px0, int px1, int py0,
-                                               int py1, Fn&& fn) {
+                                               int py1, const Lattice& Lat, long long cube, Fn&& fn) {
   int sx0, sx1, sy0, sy1;
   const bool wrap = (!PERSP) && F.wrap;
   const float axa = P.axh + P.axl, aya = P.ayh + P.ayl;  // approximate anchor, for ranges only
@@ -60,9 +59,27 @@ __device__ __forceinline__ void cube_fragments(const CubeProj& P, const FrameDev
           row_span(t, erow, lo, hi);
           const int xa = max(qx0, (int)ceilf(fmaxf(lo + ax, -1.0e9f)));
           const int xb = min(qx1, (int)floorf(fminf(hi + ax, 1.0e9f)));
+          const bool check = EXACT && may_need_exact(t, F.sigma_units);
           for (int px = xa; px <= xb; ++px) {
-            const float v = tet_value<PERSP>(t, rel_coord(px, shx, P.axh, P.axl), erow, prow);
-            if (v > 0.0f) fn(px, py, v);
+            const float X = rel_coord(px, shx, P.axh, P.axl);
+            const float v = tet_value<PERSP>(t, X, erow, prow);
+            if (!(v > 0.0f)) continue;
+            if (check) {
+              // same ill-conditioning test as the tile raster: the steepness of the
+              // active edge bounds the FP32 round-off of this value
+              float sa = t.st[0], mn = fmaf(t.a[0], X, erow[0]);
+#pragma unroll
+              for (int e = 1; e < 4; ++e) {
+                const float fe = fmaf(t.a[e], X, erow[e]);
+                if (fe < mn) { mn = fe; sa = t.st[e]; }
+              }
+              if (sa * kFragErr * v > kFragTol * fmaxf(v, F.sigma_units)) {
+                const double ex = exact_fragment(Lat, F, cube, s, sx, sy, px, py, F.m_tet);
+                fn(px, py, (float)(ex / F.unit));
+                continue;
+              }
+            }
+            fn(px, py, v);
           }
         }
       }
@@ -75,150 +92,6 @@ __device__ __forceinline__ float ray_len(const FrameDev& F, int px, int py) {
   const float xt = F.tan_x * (2.0f * ((float)px + 0.5f) / (float)F.W - 1.0f);
   const float yt = F.tan_y * (2.0f * ((float)py + 0.5f) / (float)F.H - 1.0f);
   return sqrtf(1.0f + xt * xt + yt * yt);
-}
-
-// ---------------------------------------------------------------------------
-// Persistent tile raster.
-
-template <bool ANY_PERSP>
-__global__ void k_raster(RasterArgs a) {
-  extern __shared__ unsigned smem[];
-  const int T = a.tile;
-  unsigned* acc_lo = smem;
-  unsigned* acc_hi = smem + T * T;
-  __shared__ unsigned long long item_s;
-  __shared__ double mass_w[32];
-  const int nthr = blockDim.x;
-  for (;;) {
-    if (threadIdx.x == 0) item_s = atomicAdd(&a.ctr->work_next, 1ull);
-    for (int i = threadIdx.x; i < 2 * T * T; i += nthr) smem[i] = 0u;
-    __syncthreads();
-    const unsigned long long item = item_s;
-    if (item >= (unsigned long long)a.n_items) break;
-    const long long tg = (long long)a.work[item];
-    const FrameDev* Fp = a.frames;
-    // frame of this tile: frames share one tile grid
-    const long long tpf = (long long)Fp[0].tiles_x * Fp[0].tiles_y;
-    const int f = (int)(tg / tpf);
-    const FrameDev& F = Fp[f];
-    const long long tl = tg - (long long)f * tpf;
-    const int tyi = (int)(tl / F.tiles_x), txi = (int)(tl - (long long)tyi * F.tiles_x);
-    const int px0 = txi * T, py0 = tyi * T;
-    const int px1 = min(px0 + T, F.W) - 1, py1 = min(py0 + T, F.H) - 1;
-    const unsigned long long e0 = a.off[tg], e1 = a.off[tg + 1];
-    bool dummy = true;
-    for (unsigned long long e = e0 + threadIdx.x; e < e1; e += nthr) {
-      const long long cube = (long long)a.list[e];
-      CubeProj P;
-      auto acc = [&](int px, int py, float v) {
-        const int li = (py - py0) * T + (px - px0);
-        accum_fixed(&acc_lo[li], &acc_hi[li], v, &a.ctr->errors);
-      };
-      if (ANY_PERSP && F.persp) {
-        if (!project_cube<true>(a.L, F, cube, P, dummy)) continue;
-        cube_fragments<true>(P, F, px0, px1, py0, py1, acc);
-      } else {
-        if (!project_cube<false>(a.L, F, cube, P, dummy)) continue;
-        cube_fragments<false>(P, F, px0, px1, py0, py1, acc);
-      }
-    }
-    __syncthreads();
-    // one store per pixel, and the tile's share of the frame mass
-    double msum = 0.0;
-    const int tw = px1 - px0 + 1, th = py1 - py0 + 1;
-    float* img = a.image + (long long)f * a.image_stride;
-    for (int li = threadIdx.x; li < tw * th; li += nthr) {
-      const int ly = li / tw, lx = li - ly * tw;
-      const int si = ly * T + lx;
-      const unsigned long long q = ((unsigned long long)acc_hi[si] << 16) + (unsigned long long)acc_lo[si];
-      double v = (double)q * F.unit;
-      if (ANY_PERSP && F.persp) v *= (double)ray_len(F, px0 + lx, py0 + ly);
-      const float vf = (float)v;
-      img[(long long)(py0 + ly) * F.W + (px0 + lx)] = vf;
-      msum += (double)vf;
-    }
-    // fixed-shape reduction: warp shuffles, then warp 0 over the warp sums
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) msum += __shfl_down_sync(0xffffffffu, msum, o);
-    if ((threadIdx.x & 31) == 0) mass_w[threadIdx.x >> 5] = msum;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double w = threadIdx.x < (unsigned)(nthr >> 5) ? mass_w[threadIdx.x] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
-      if (threadIdx.x == 0) a.mass_tile[tg] = w * F.pix_area;
-    }
-    __syncthreads();
-  }
-}
-
-int raster_max_ctas_per_sm(int threads, int tile, int any_persp) {
-  int n = 0;
-  const size_t smem = sizeof(unsigned) * 2 * tile * tile;
-  if (any_persp)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster<true>, threads, smem);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster<false>, threads, smem);
-  return n < 1 ? 1 : n;
-}
-
-cudaError_t launch_raster(const RasterArgs& a, int ctas, int threads, int any_persp, cudaStream_t s) {
-  const size_t smem = sizeof(unsigned) * 2 * a.tile * a.tile;
-  if (any_persp) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_raster<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_raster<true><<<ctas, threads, smem, s>>>(a);
-  } else {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_raster<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_raster<false><<<ctas, threads, smem, s>>>(a);
-  }
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Fragment counter over the same bins (chord > 0 pairs).
-
-__global__ void k_count(RasterArgs a, unsigned long long* __restrict__ counts) {
-  __shared__ unsigned long long item_s;
-  for (;;) {
-    if (threadIdx.x == 0) item_s = atomicAdd(&a.ctr->work_next, 1ull);
-    __syncthreads();
-    const unsigned long long item = item_s;
-    __syncthreads();
-    if (item >= (unsigned long long)a.n_items) break;
-    const long long tg = (long long)a.work[item];
-    const long long tpf = (long long)a.frames[0].tiles_x * a.frames[0].tiles_y;
-    const int f = (int)(tg / tpf);
-    const FrameDev& F = a.frames[f];
-    const long long tl = tg - (long long)f * tpf;
-    const int tyi = (int)(tl / F.tiles_x), txi = (int)(tl - (long long)tyi * F.tiles_x);
-    const int T = a.tile;
-    const int px0 = txi * T, py0 = tyi * T;
-    const int px1 = min(px0 + T, F.W) - 1, py1 = min(py0 + T, F.H) - 1;
-    unsigned long long n = 0;
-    bool dummy = true;
-    for (unsigned long long e = a.off[tg] + threadIdx.x; e < a.off[tg + 1]; e += blockDim.x) {
-      const long long cube = (long long)a.list[e];
-      CubeProj P;
-      auto cnt = [&](int, int, float) { ++n; };
-      if (F.persp) {
-        if (!project_cube<true>(a.L, F, cube, P, dummy)) continue;
-        cube_fragments<true>(P, F, px0, px1, py0, py1, cnt);
-      } else {
-        if (!project_cube<false>(a.L, F, cube, P, dummy)) continue;
-        cube_fragments<false>(P, F, px0, px1, py0, py1, cnt);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n += __shfl_down_sync(0xffffffffu, n, o);
-    if ((threadIdx.x & 31) == 0 && n) atomicAdd(&counts[f], n);
-  }
-}
-
-cudaError_t launch_count_fragments(const RasterArgs& a, unsigned long long* d_counts, int n_frames, int ctas,
-                                   int threads, cudaStream_t s) {
-  (void)n_frames;
-  k_count<<<ctas, threads, 0, s>>>(a, d_counts);
-  return cudaGetLastError();
 }
 
 // Per-frame mass: fixed-order sum of the frame's tile partials.
@@ -255,7 +128,7 @@ __device__ __forceinline__ void atomic_cube(const Lattice& L, const FrameDev& F,
   bool ok = true;
   if (!project_cube<PERSP>(L, F, cube, P, ok)) return;
   const double unit = F.unit;
-  cube_fragments<PERSP>(P, F, 0, F.W - 1, 0, F.H - 1, [&](int px, int py, float v) {
+  cube_fragments<PERSP, true>(P, F, 0, F.W - 1, 0, F.H - 1, L, cube, [&](int px, int py, float v) {
     float val = (float)((double)v * unit);
     if (PERSP) val *= ray_len(F, px, py);
     atomicAdd(&img[(long long)py * F.W + px], val);
