@@ -93,7 +93,7 @@ typedef struct {
 /* Tuning knobs (lt_autotune fills them; zero fields take defaults). */
 typedef struct {
   int tile;           /* screen tile edge in pixels: 8, 16, 32 or 64 (default 16) */
-  int raster_threads; /* threads per raster CTA: 64..1024, multiple of 32 (default 256) */
+  int raster_threads; /* threads per raster CTA: 64..256, multiple of 32 (default 256) */
   int ctas_per_sm;    /* persistent raster CTAs per SM (default: occupancy limit) */
   int frac_bits;      /* fixed-point fraction bits relative to the mean column density (default 28) */
 } lt_config;

@@ -89,7 +89,7 @@ lt_config default_config() {
 
 bool valid_config(const lt_config& c) {
   const bool tile_ok = c.tile == 0 || c.tile == 8 || c.tile == 16 || c.tile == 32 || c.tile == 64;
-  const bool thr_ok = c.raster_threads == 0 || (c.raster_threads >= 64 && c.raster_threads <= 1024 &&
+  const bool thr_ok = c.raster_threads == 0 || (c.raster_threads >= 64 && c.raster_threads <= 256 &&
                                                 c.raster_threads % 32 == 0);
   const bool cps_ok = c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32;
   const bool fb_ok = c.frac_bits == 0 || (c.frac_bits >= 8 && c.frac_bits <= 40);
@@ -651,7 +651,7 @@ lt_status lt_autotune(lt_ctx* ctx, const lt_camera* cams, int n_frames, const in
   cudaStream_t s = (cudaStream_t)stream;
   const lt_config base = ctx->cfg;
   const int tiles[] = {16, 32};
-  const int threads[] = {128, 256, 512};
+  const int threads[] = {128, 256};
   float best_ms = 1e30f;
   lt_config best_cfg = base;
   cudaEvent_t e0, e1;

@@ -289,6 +289,7 @@ static size_t tile_smem(int threads, int tile) {
 }
 
 int raster_max_ctas_per_sm(int threads, int tile, int any_persp) {
+  if (threads > 256 || threads % 32) return 0;  // the kernel is compiled for at most 256 threads
   int n = 0;
   const size_t smem = tile_smem(threads, tile);
   cudaError_t e;
