@@ -508,6 +508,7 @@ lt_status lt_build_tets(lt_ctx* ctx, const void* d_pos, int pos_fmt, int N, floa
   L.h = box / (float)N;
   L.half_box = 0.5f * box;
   L.n_particles = (long long)N * N * N;
+  lt::lattice_set_divisor(L, N);
   ctx->L = L;
   ctx->n_snap = n_snapshots;
   ctx->total_mass = total_mass;

@@ -75,8 +75,39 @@ struct Lattice {
   int fmt;          // 0 float4 wrapped positions, 1 half4 offsets in cell units
   int N;
   float box, h, half_box;
-  long long n_particles;  // N^3
+  long long n_particles;  // N^3 (< 2^31)
+  // unsigned division by N as a multiply-high and two shifts (Granlund and
+  // Montgomery, "Division by invariant integers using multiplication", 1994,
+  // Fig. 4.1): q = (t + ((n - t) >> s1)) >> s2, t = umulhi(div_m, n)
+  unsigned div_m;
+  int div_s1, div_s2;
 };
+
+// Host: fill the division constants for divisor N >= 1 (exact for every
+// 32-bit dividend).
+inline void lattice_set_divisor(Lattice& L, int N) {
+  int l = 0;
+  while ((1ull << l) < (unsigned long long)N) ++l;  // l = ceil(log2 N)
+  L.div_m = (unsigned)((((1ull << l) - (unsigned long long)N) << 32) / (unsigned long long)N + 1ull);
+  L.div_s1 = l < 1 ? l : 1;
+  L.div_s2 = l > 1 ? l - 1 : 0;
+}
+
+__device__ __forceinline__ unsigned div_n(const Lattice& L, unsigned n) {
+  const unsigned t = __umulhi(L.div_m, n);
+  return (t + ((n - t) >> L.div_s1)) >> L.div_s2;
+}
+
+// Lattice indices of a cube (= of its corner-0 particle) from its id.
+__device__ __forceinline__ void cube_ijk(const Lattice& L, long long cube, int& i, int& j, int& k) {
+  const unsigned c = (unsigned)cube;
+  const unsigned q = div_n(L, c);
+  const unsigned N = (unsigned)L.N;
+  i = (int)(c - q * N);
+  const unsigned q2 = div_n(L, q);
+  j = (int)(q - q2 * N);
+  k = (int)q2;
+}
 
 // One view in kernel form.
 struct FrameDev {
@@ -113,7 +144,8 @@ struct FrameDev {
 // Lattice addressing (Eq. 8) and the unwrapped corner positions.
 
 __device__ __forceinline__ long long particle_id(int i, int j, int k, int N) {
-  return (long long)i + (long long)N * ((long long)j + (long long)N * k);
+  // N^3 < 2^31: the in-snapshot index fits in 32 bits
+  return (long long)(unsigned)(i + N * (j + N * k));
 }
 
 // Minimum-image displacement of a wrapped coordinate p from its wrapped
@@ -209,10 +241,8 @@ __device__ __forceinline__ float rel_coord(int p, int shift, float ah, float al)
 template <bool PERSP>
 __device__ __forceinline__ bool project_cube(const Lattice& L, const FrameDev& F, long long cube, CubeProj& P,
                                              bool& finite_ok, bool* straddle = nullptr) {
-  const int N = L.N;
-  const int i = (int)(cube % N);
-  const int j = (int)((cube / N) % N);
-  const int k = (int)(cube / ((long long)N * N));
+  int i, j, k;
+  cube_ijk(L, cube, i, j, k);
   const long long snap_off = (long long)F.snapshot * L.n_particles;
   bool ok = true;
   if (!PERSP) {
@@ -301,10 +331,8 @@ struct TetProj {
 // of a perspective eye (those cubes are counted by the bin pass).
 template <bool PERSP>
 __device__ __forceinline__ bool project_tet(const Lattice& L, const FrameDev& F, long long cube, int s, TetProj& P) {
-  const int N = L.N;
-  const int i = (int)(cube % N);
-  const int j = (int)((cube / N) % N);
-  const int k = (int)(cube / ((long long)N * N));
+  int i, j, k;
+  cube_ijk(L, cube, i, j, k);
   const long long snap_off = (long long)F.snapshot * L.n_particles;
   bool ok = true;
   if (!PERSP) {

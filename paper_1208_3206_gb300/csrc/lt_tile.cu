@@ -22,12 +22,14 @@
 
 namespace lt {
 
-constexpr int kRec = 32;  // words per tetrahedron record
+constexpr int kRec = 36;  // words per tetrahedron record (stride 4 mod 32: float4 access is conflict-free)
 constexpr int kQueue = 2048;  // ill-conditioned fragments queued per tile
 
-// Record words: 0-11 edge functions (a[4], b[4], c[4]); 12-18 perspective
-// depth planes and g; 19 qx0, 20 qy0, 21 box width, 22 1/width; 23-26 edge
-// steepness, 27 its maximum; 28-29 periodic copy (sx, sy).
+// Record layout, in float4 groups so the walk reads it with a few 128-bit
+// loads: [0] qx0, qy0, box width, 1/width; [1] a[4]; [2] b[4]; [3] c[4] (edge
+// functions); [4] pa0, pb0, pc0, pa1; [5] pb1, pc1, g, exact-check flag
+// (perspective depth planes); [6] edge steepness st[4]; [7] periodic copy
+// (sx, sy). Words 30-35 pad the stride.
 
 constexpr float kErr = kFragErr;
 constexpr float kTol = kFragTol;
@@ -40,7 +42,7 @@ __device__ __forceinline__ unsigned long long pack_frag(unsigned tau, int sx, in
 
 template <bool ANY_PERSP, bool COUNT>
 __global__ void __launch_bounds__(256, 2) k_tile(RasterArgs a, unsigned long long* __restrict__ counts) {
-  extern __shared__ float smem_f[];
+  extern __shared__ __align__(16) float smem_f[];
   const int T = a.tile;
   const int nw = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -80,14 +82,19 @@ __global__ void __launch_bounds__(256, 2) k_tile(RasterArgs a, unsigned long lon
     const float Kn0 = 6.0f * F.K;
     const float sig = F.sigma_units;
 
+    // tb / 6 and tb % 6 carried along the loop (tb advances by nw * 32)
+    const unsigned step_q = (unsigned)(nw * 32) / 6u, step_r = (unsigned)(nw * 32) % 6u;
+    unsigned long long cq = (unsigned long long)warp * 32u / 6u;
+    unsigned cr = (unsigned)(warp * 32) % 6u;
     for (long long tb = (long long)warp * 32; tb < ntet; tb += (long long)nw * 32) {
       // ---- 1. one tetrahedron per lane
       const long long tau = tb + lane;
       TetProj P;
       bool ok = false;
       if (tau < ntet) {
-        const long long cube = (long long)a.list[e0 + (unsigned long long)(tau / 6)];
-        const int s = (int)(tau % 6);
+        const unsigned rel = cr + (unsigned)lane;  // < 38
+        const long long cube = (long long)a.list[e0 + cq + rel / 6u];
+        const int s = (int)(rel % 6u);
         ok = persp ? project_tet<true>(a.L, F, cube, s, P) : project_tet<false>(a.L, F, cube, s, P);
       }
       float bx0 = 0.f, bx1 = -1.f, by0 = 0.f, by1 = -1.f;
@@ -129,28 +136,21 @@ __global__ void __launch_bounds__(256, 2) k_tile(RasterArgs a, unsigned long lon
                                                Kn, P.w0, invKn, t)
                              : tet_setup<false>(x0, y0, x1, y1, x2, y2, x3, y3, 0.f, 0.f, 0.f, 0.f, Kn, 0.f, 0.f, t);
             if (set) {
-              float* R = recs + lane * kRec;
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                R[e] = t.a[e];
-                R[4 + e] = t.b[e];
-                R[8 + e] = t.c[e];
-                R[23 + e] = t.st[e];
-              }
-              if (persp) {
-                R[12] = t.pa[0]; R[13] = t.pa[1];
-                R[14] = t.pb[0]; R[15] = t.pb[1];
-                R[16] = t.pc[0]; R[17] = t.pc[1];
-                R[18] = t.g;
-              }
+              float4* R = reinterpret_cast<float4*>(recs + lane * kRec);
               const int qw = qx1 - qx0 + 1;
-              R[19] = __int_as_float(qx0);
-              R[20] = __int_as_float(qy0);
-              R[21] = __int_as_float(qw);
-              R[22] = 1.0f / (float)qw;
-              R[27] = may_need_exact(t, sig) ? 1.0f : 0.0f;
-              R[28] = __int_as_float(sx);
-              R[29] = __int_as_float(sy);
+              R[0] = make_float4(__int_as_float(qx0), __int_as_float(qy0), __int_as_float(qw), 1.0f / (float)qw);
+              R[1] = make_float4(t.a[0], t.a[1], t.a[2], t.a[3]);
+              R[2] = make_float4(t.b[0], t.b[1], t.b[2], t.b[3]);
+              R[3] = make_float4(t.c[0], t.c[1], t.c[2], t.c[3]);
+              const float flag = may_need_exact(t, sig) ? 1.0f : 0.0f;
+              if (persp) {
+                R[4] = make_float4(t.pa[0], t.pb[0], t.pc[0], t.pa[1]);
+                R[5] = make_float4(t.pb[1], t.pc[1], t.g, flag);
+              } else {
+                R[5] = make_float4(0.f, 0.f, 0.f, flag);
+              }
+              R[6] = make_float4(t.st[0], t.st[1], t.st[2], t.st[3]);
+              R[7] = make_float4(__int_as_float(sx), __int_as_float(sy), 0.f, 0.f);
               n = qw * (qy1 - qy0 + 1);
             }
           }
@@ -178,31 +178,39 @@ __global__ void __launch_bounds__(256, 2) k_tile(RasterArgs a, unsigned long lon
           const int own_off = __shfl_sync(FULL, off, owner);
           const int pos = base + lane;
           if (pos < total) {
-            const float* R = recs + owner * kRec;
+            const float4* R = reinterpret_cast<const float4*>(recs + owner * kRec);
             const int kk = pos - own_off;
-            const int w = __float_as_int(R[21]);
-            const int dy = (int)(((float)kk + 0.5f) * R[22]);
+            const float4 r0 = R[0];
+            const int w = __float_as_int(r0.z);
+            const int dy = (int)(((float)kk + 0.5f) * r0.w);
             const int dx = kk - dy * w;
-            const int X = __float_as_int(R[19]) + dx, Y = __float_as_int(R[20]) + dy;
+            const int X = __float_as_int(r0.x) + dx, Y = __float_as_int(r0.y) + dy;
             const float fx = (float)X, fy = (float)Y;
-            const float f0 = fmaf(R[0], fx, fmaf(R[4], fy, R[8]));
-            const float f1 = fmaf(R[1], fx, fmaf(R[5], fy, R[9]));
-            const float f2 = fmaf(R[2], fx, fmaf(R[6], fy, R[10]));
-            const float f3 = fmaf(R[3], fx, fmaf(R[7], fy, R[11]));
+            const float4 ra = R[1], rb = R[2], rc = R[3];
+            const float f0 = fmaf(ra.x, fx, fmaf(rb.x, fy, rc.x));
+            const float f1 = fmaf(ra.y, fx, fmaf(rb.y, fy, rc.y));
+            const float f2 = fmaf(ra.z, fx, fmaf(rb.z, fy, rc.z));
+            const float f3 = fmaf(ra.w, fx, fmaf(rb.w, fy, rc.w));
             const float Tv = fmaxf(fminf(fminf(f0, f1), fminf(f2, f3)), 0.0f);
             float v = Tv;
+            float4 r5;
             if (persp) {
-              const float M = fmaxf(fmaf(R[12], fx, fmaf(R[14], fy, R[16])), fmaf(R[13], fx, fmaf(R[15], fy, R[17])));
-              v = __fdividef(Tv, M * fmaf(R[18], Tv, M));
+              const float4 r4 = R[4];
+              r5 = R[5];
+              const float M = fmaxf(fmaf(r4.x, fx, fmaf(r4.y, fy, r4.z)), fmaf(r4.w, fx, fmaf(r5.x, fy, r5.y)));
+              v = __fdividef(Tv, M * fmaf(r5.z, Tv, M));
+            } else if (!COUNT) {
+              r5 = R[5];
             }
             if (v > 0.0f) {
               bool risky = false;
-              if (!COUNT && R[27] != 0.0f) {
+              if (!COUNT && r5.w != 0.0f) {
                 // steepness of the edge that bounds the value here
-                float sa = R[23], mn = f0;
-                if (f1 < mn) { mn = f1; sa = R[24]; }
-                if (f2 < mn) { mn = f2; sa = R[25]; }
-                if (f3 < mn) { sa = R[26]; }
+                const float4 r6 = R[6];
+                float sa = r6.x, mn = f0;
+                if (f1 < mn) { mn = f1; sa = r6.y; }
+                if (f2 < mn) { mn = f2; sa = r6.z; }
+                if (f3 < mn) { sa = r6.w; }
                 risky = sa * kErr * v > kTol * fmaxf(v, sig);
               }
               if (COUNT) {
@@ -210,7 +218,8 @@ __global__ void __launch_bounds__(256, 2) k_tile(RasterArgs a, unsigned long lon
               } else if (!risky) {
                 accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], v, &a.ctr->errors);
               } else {
-                const int sxo = __float_as_int(R[28]), syo = __float_as_int(R[29]);
+                const float4 r7 = R[7];
+                const int sxo = __float_as_int(r7.x), syo = __float_as_int(r7.y);
                 const unsigned slot = atomicAdd(&qn, 1u);
                 if (slot < (unsigned)kQueue) {
                   queue[slot] = pack_frag((unsigned)(tb + owner), sxo, syo, X, Y);
@@ -225,6 +234,9 @@ __global__ void __launch_bounds__(256, 2) k_tile(RasterArgs a, unsigned long lon
           __syncwarp();
         }
       }
+      cr += step_r;
+      cq += step_q + (cr >= 6u ? 1u : 0u);
+      cr = cr >= 6u ? cr - 6u : cr;
     }
     if (COUNT) {
       unsigned long long c = nfrag;
