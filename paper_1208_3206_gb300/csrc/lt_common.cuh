@@ -217,7 +217,7 @@ __device__ __forceinline__ void ff_project(float Xh, float Xl, float Zh, float Z
   const float q = Xh / Zh;
   float r = fmaf(-q, Zh, Xh);  // exact residual of the division
   r = fmaf(-q, Zl, Xl) + r;
-  const float ql = r / Zh;
+  const float ql = __fdividef(r, Zh);  // low part: a few ulp suffice
   const float p = kh * q;
   float e = fmaf(kh, q, -p);   // exact product error
   e = fmaf(kh, ql, e);
@@ -266,7 +266,7 @@ __device__ __forceinline__ bool project_cube(const Lattice& L, const FrameDev& F
       ff_project(Xh, Xl, Zh, Zl, F.kxh, F.kxl, F.cx, P.axh, P.axl);
       ff_project(Yh, Yl, Zh, Zl, F.kyh, F.kyl, F.cy, P.ayh, P.ayl);
     }
-    const float iZ0 = 1.0f / Z0;
+    const float iZ0 = __frcp_rn(Z0);
     P.w0 = iZ0;
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
@@ -277,7 +277,7 @@ __device__ __forceinline__ bool project_cube(const Lattice& L, const FrameDev& F
       const float Zn = Z0 + dZ;
       front = front && (Zn > F.near_z);
       n_front += Zn > F.near_z ? 1 : 0;
-      const float inv = 1.0f / (Zn * Z0);
+      const float inv = __frcp_rn(Zn * Z0);
       // X_n/Z_n - X0/Z0 = (dX Z0 - X0 dZ) / (Z_n Z0), free of cancellation
       P.x[n] = (dX * Z0 - X0 * dZ) * inv * F.kx;
       P.y[n] = (dY * Z0 - Y0 * dZ) * inv * F.ky;
@@ -357,7 +357,7 @@ __device__ __forceinline__ bool project_tet(const Lattice& L, const FrameDev& F,
   bool front = Z0 > F.near_z;
   ff_project(Xh, Xl, Zh, Zl, F.kxh, F.kxl, F.cx, P.axh, P.axl);
   ff_project(Yh, Yl, Zh, Zl, F.kyh, F.kyl, F.cy, P.ayh, P.ayl);
-  P.w0 = 1.0f / Z0;
+  P.w0 = __frcp_rn(Z0);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const float3 l = load_corner(L, snap_off, i, j, k, tet_corner_dyn(s, c), ok);
@@ -366,7 +366,7 @@ __device__ __forceinline__ bool project_tet(const Lattice& L, const FrameDev& F,
     const float dZ = F.f[0] * l.x + F.f[1] * l.y + F.f[2] * l.z;
     const float Zn = Z0 + dZ;
     front = front && (Zn > F.near_z);
-    const float inv = 1.0f / (Zn * Z0);
+    const float inv = __frcp_rn(Zn * Z0);
     P.x[c] = (dX * Z0 - X0 * dZ) * inv * F.kx;
     P.y[c] = (dY * Z0 - Y0 * dZ) * inv * F.ky;
     P.dw[c] = -dZ * inv;
@@ -407,7 +407,7 @@ __device__ __forceinline__ void cswap(bool s, float& p, float& q) {
 __device__ __forceinline__ void edge_fn(float xj, float yj, float ex, float ey, float o1, float o2, float Wn,
                                         float tiny, float& a, float& b, float& c) {
   const float prod = fmaxf(fabsf(o1 * o2), tiny);
-  float w = Wn / prod;
+  float w = __fdividef(Wn, prod);  // prod is far below 2^126
   w = (o1 + o2) < 0.0f ? -w : w;
   const bool dead = (o1 == 0.0f) && (o2 == 0.0f);  // zero-length edge or flat hull
   a = dead ? 0.0f : -ey * w;
@@ -425,7 +425,7 @@ __device__ __forceinline__ bool face_plane(float xp, float yp, float wp, float x
   const float ny = uw * vx - ux * vw;
   // a face seen nearly edge-on has an unreliable FP32 slope: treat as vertical
   if (!(fabsf(nw) > 1e-5f * (fabsf(ux * vy) + fabsf(uy * vx)))) return false;
-  const float inw = 1.0f / nw;
+  const float inw = __frcp_rn(nw);
   pa = -nx * inw;
   pb = -ny * inw;
   pc = wp - pa * xp - pb * yp;
@@ -544,7 +544,7 @@ __device__ __forceinline__ bool tet_setup(float x0, float y0, float x1, float y1
     const EdgeRef r = edge_ref(K, e);
     edge_fn(sel4(K.x, r.j), sel4(K.y, r.j), r.ex, r.ey, r.o1, r.o2, Kn, tiny, t.a[e], t.b[e], t.c[e]);
     const float omin = fminf(fabsf(r.o1), fabsf(r.o2));
-    t.st[e] = (r.ex * r.ex + r.ey * r.ey) / fmaxf(omin, tiny);
+    t.st[e] = __fdividef(r.ex * r.ex + r.ey * r.ey, fmaxf(omin, tiny));
   }
   if (!K.caseB) {
     t.a[3] = 0.0f;
@@ -553,10 +553,10 @@ __device__ __forceinline__ bool tet_setup(float x0, float y0, float x1, float y1
     t.st[3] = 0.0f;
   }
   // pyramid apex value 2 Kn / S; the perspective depth factor is at most 1 / w_min^2
-  t.hmax = 2.0f * Kn / K.S;
+  t.hmax = __fdividef(2.0f * Kn, K.S);
   if (PERSP) {
     const float wmin = wa + fminf(fminf(w0, w1), fminf(w2, w3));
-    t.hmax = t.hmax / (wmin * wmin);
+    t.hmax = __fdividef(t.hmax, wmin * wmin);
   }
   if (PERSP) {
     const float* X = K.x;

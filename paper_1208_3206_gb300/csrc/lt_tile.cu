@@ -26,10 +26,10 @@ constexpr int kRec = 36;  // words per tetrahedron record (stride 4 mod 32: floa
 constexpr int kQueue = 2048;  // ill-conditioned fragments queued per tile
 
 // Record layout, in float4 groups so the walk reads it with a few 128-bit
-// loads: [0] qx0, qy0, box width, 1/width; [1] a[4]; [2] b[4]; [3] c[4] (edge
-// functions); [4] pa0, pb0, pc0, pa1; [5] pb1, pc1, g, exact-check flag
-// (perspective depth planes); [6] edge steepness st[4]; [7] periodic copy
-// (sx, sy). Words 30-35 pad the stride.
+// loads: [0] qx0, qy0, qx1 (bounding box in tile pixels); [1] a[4]; [2] b[4];
+// [3] c[4] (edge functions); [4] 1/a[4] (row spans); [5] pa0, pb0, pc0, pa1;
+// [6] pb1, pc1, g (perspective depth planes), exact-check flag; [7] edge
+// steepness st[4]; [8] periodic copy (sx, sy).
 
 constexpr float kErr = kFragErr;
 constexpr float kTol = kFragTol;
@@ -40,8 +40,38 @@ __device__ __forceinline__ unsigned long long pack_frag(unsigned tau, int sx, in
          ((unsigned long long)(unsigned)Y << 52);
 }
 
+// 1 / a, or 0 for a == 0 (an edge function constant along the row).
+__device__ __forceinline__ float inv_or_zero(float a) { return a != 0.0f ? __frcp_rn(a) : 0.0f; }
+
+// Narrow [lo, hi] to the X where a X + rr >= 0 (rr the row term b Y + c).
+// An edge constant along the row (a == 0) empties the row when rr < 0; the
+// unused slot (rr = +inf) never constrains.
+__device__ __forceinline__ void span_edge(float a, float rr, float ia, float& lo, float& hi) {
+  const float xe = -rr * ia;
+  if (a > 0.0f) lo = fmaxf(lo, xe);
+  if (a < 0.0f) hi = fminf(hi, xe);
+  if (a == 0.0f && rr < 0.0f) hi = __int_as_float(0xff800000);
+}
+
+// Exclusive warp scan of n; total receives the warp's sum.
+__device__ __forceinline__ int warp_excl_scan(int n, int& total) {
+  const int lane = threadIdx.x & 31;
+  int incl = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  total = __shfl_sync(0xffffffffu, incl, 31);
+  return incl - n;
+}
+
+#ifndef LT_TILE_MIN_CTAS
+#define LT_TILE_MIN_CTAS 2  // resident 256-thread CTAs per SM the register budget is cut for
+#endif
+
 template <bool ANY_PERSP, bool COUNT>
-__global__ void __launch_bounds__(256, 2) k_tile(RasterArgs a, unsigned long long* __restrict__ counts) {
+__global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, unsigned long long* __restrict__ counts) {
   extern __shared__ __align__(16) float smem_f[];
   const int T = a.tile;
   const int nw = blockDim.x >> 5;
@@ -49,7 +79,7 @@ __global__ void __launch_bounds__(256, 2) k_tile(RasterArgs a, unsigned long lon
   unsigned* acc_lo = reinterpret_cast<unsigned*>(smem_f);
   unsigned* acc_hi = acc_lo + T * T;
   float* recs = reinterpret_cast<float*>(acc_hi + T * T) + warp * 32 * kRec;
-  int* starts = reinterpret_cast<int*>(reinterpret_cast<float*>(acc_hi + T * T) + nw * 32 * kRec) + warp * 32;
+  int4* jobs = reinterpret_cast<int4*>(reinterpret_cast<float*>(acc_hi + T * T) + nw * 32 * kRec) + warp * 32;
   __shared__ unsigned long long item_s;
   __shared__ double mass_w[32];
   __shared__ unsigned long long queue[kQueue];
@@ -114,124 +144,152 @@ __global__ void __launch_bounds__(256, 2) k_tile(RasterArgs a, unsigned long lon
       const int rounds = __reduce_max_sync(FULL, ncp);
       float Kn = Kn0, invKn = 0.f;
       if (persp && ok) {
-        Kn = Kn0 / (P.z[0] * P.z[1] * P.z[2] * P.z[3]);
-        invKn = 1.0f / Kn;
+        Kn = __fdividef(Kn0, P.z[0] * P.z[1] * P.z[2] * P.z[3]);
+        invKn = __frcp_rn(Kn);
       }
       for (int r = 0; r < rounds; ++r) {
-        int n = 0;
+        int nrows = 0, qx0 = 0, qx1 = 0, qy0 = 0, sx = 0, sy = 0;
+        TetRaster t;
         if (r < ncp) {
-          const int sx = sx0 + r % ncx, sy = sy0 + r / ncx;
+          sx = sx0 + r % ncx;
+          sy = sy0 + r / ncx;
           // vertex coordinates relative to the tile origin: anchor + shift - tile corner
           const float ox = ((float)(tx0 - sx * F.W) - P.axh) - P.axl;
           const float oy = ((float)(ty0 - sy * F.H) - P.ayh) - P.ayl;
           const float x0 = P.x[0] - ox, x1 = P.x[1] - ox, x2 = P.x[2] - ox, x3 = P.x[3] - ox;
           const float y0 = P.y[0] - oy, y1 = P.y[1] - oy, y2 = P.y[2] - oy, y3 = P.y[3] - oy;
-          const int qx0 = max(0, (int)ceilf(bx0 - ox - 1e-3f));
-          const int qx1 = min(tw - 1, (int)floorf(bx1 - ox + 1e-3f));
-          const int qy0 = max(0, (int)ceilf(by0 - oy - 1e-3f));
+          qx0 = max(0, (int)ceilf(bx0 - ox - 1e-3f));
+          qx1 = min(tw - 1, (int)floorf(bx1 - ox + 1e-3f));
+          qy0 = max(0, (int)ceilf(by0 - oy - 1e-3f));
           const int qy1 = min(th - 1, (int)floorf(by1 - oy + 1e-3f));
           if (qx0 <= qx1 && qy0 <= qy1) {
-            TetRaster t;
-            bool set = persp ? tet_setup<true>(x0, y0, x1, y1, x2, y2, x3, y3, P.dw[0], P.dw[1], P.dw[2], P.dw[3],
-                                               Kn, P.w0, invKn, t)
-                             : tet_setup<false>(x0, y0, x1, y1, x2, y2, x3, y3, 0.f, 0.f, 0.f, 0.f, Kn, 0.f, 0.f, t);
-            if (set) {
-              float4* R = reinterpret_cast<float4*>(recs + lane * kRec);
-              const int qw = qx1 - qx0 + 1;
-              R[0] = make_float4(__int_as_float(qx0), __int_as_float(qy0), __int_as_float(qw), 1.0f / (float)qw);
-              R[1] = make_float4(t.a[0], t.a[1], t.a[2], t.a[3]);
-              R[2] = make_float4(t.b[0], t.b[1], t.b[2], t.b[3]);
-              R[3] = make_float4(t.c[0], t.c[1], t.c[2], t.c[3]);
-              const float flag = may_need_exact(t, sig) ? 1.0f : 0.0f;
-              if (persp) {
-                R[4] = make_float4(t.pa[0], t.pb[0], t.pc[0], t.pa[1]);
-                R[5] = make_float4(t.pb[1], t.pc[1], t.g, flag);
-              } else {
-                R[5] = make_float4(0.f, 0.f, 0.f, flag);
-              }
-              R[6] = make_float4(t.st[0], t.st[1], t.st[2], t.st[3]);
-              R[7] = make_float4(__int_as_float(sx), __int_as_float(sy), 0.f, 0.f);
-              n = qw * (qy1 - qy0 + 1);
-            }
+            const bool set =
+                persp ? tet_setup<true>(x0, y0, x1, y1, x2, y2, x3, y3, P.dw[0], P.dw[1], P.dw[2], P.dw[3], Kn,
+                                        P.w0, invKn, t)
+                      : tet_setup<false>(x0, y0, x1, y1, x2, y2, x3, y3, 0.f, 0.f, 0.f, 0.f, Kn, 0.f, 0.f, t);
+            if (set) nrows = qy1 - qy0 + 1;
           }
         }
-        // ---- 2. flatten the candidates of the 32 tetrahedra
-        int incl = n;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(FULL, incl, o);
-          if (lane >= o) incl += y;
+        // ---- 2. records of the drawable tetrahedra, compacted, and the
+        // flattened (tetrahedron, row) jobs
+        const unsigned lt_mask = (1u << lane) - 1u, le_mask = (2u << lane) - 1u;
+        const int slot = __popc(__ballot_sync(FULL, nrows > 0) & lt_mask);
+        int rtotal;
+        const int roff = warp_excl_scan(nrows, rtotal);
+        if (nrows > 0) {
+          float4* R = reinterpret_cast<float4*>(recs + slot * kRec);
+          R[0] = make_float4(__int_as_float(qx0), __int_as_float(qy0), __int_as_float(qx1), __int_as_float(roff));
+          R[1] = make_float4(t.a[0], t.a[1], t.a[2], t.a[3]);
+          R[2] = make_float4(t.b[0], t.b[1], t.b[2], t.b[3]);
+          R[3] = make_float4(t.c[0], t.c[1], t.c[2], t.c[3]);
+          R[4] = make_float4(inv_or_zero(t.a[0]), inv_or_zero(t.a[1]), inv_or_zero(t.a[2]), inv_or_zero(t.a[3]));
+          const float flag = may_need_exact(t, sig) ? 1.0f : 0.0f;
+          if (persp) {
+            R[5] = make_float4(t.pa[0], t.pb[0], t.pc[0], t.pa[1]);
+            R[6] = make_float4(t.pb[1], t.pc[1], t.g, flag);
+          } else {
+            R[6] = make_float4(0.f, 0.f, 0.f, flag);
+          }
+          R[7] = make_float4(t.st[0], t.st[1], t.st[2], t.st[3]);
+          R[8] = make_float4(__int_as_float(sx), __int_as_float(sy), __int_as_float(lane), 0.f);
         }
-        const int off = incl - n;
-        const int total = __shfl_sync(FULL, incl, 31);
         __syncwarp();
-        // ---- 3. walk the candidates, 32 per step
-        int carry = 0;
-        for (int base = 0; base < total; base += 32) {
-          const int bp = off - base;
-          const bool in = n > 0 && bp >= 0 && bp < 32;
-          const unsigned mask = __reduce_or_sync(FULL, in ? (1u << bp) : 0u);
-          if (in) starts[bp] = lane;
-          __syncwarp();
-          const unsigned m = mask & (FULL >> (31 - lane));
-          const int owner = m ? starts[31 - __clz(m)] : carry;
-          const int own_off = __shfl_sync(FULL, off, owner);
-          const int pos = base + lane;
-          if (pos < total) {
-            const float4* R = reinterpret_cast<const float4*>(recs + owner * kRec);
-            const int kk = pos - own_off;
+        // The owner of a position in a 32-wide step is the last run starting
+        // at or before it: with runs compacted, its index is the number of
+        // runs started before the step plus those started in the step up to
+        // the position, minus one.
+        int rprev = 0;
+        for (int rb = 0; rb < rtotal; rb += 32) {
+          const int rrel = roff - rb;
+          const unsigned rmask = __reduce_or_sync(FULL, (nrows > 0 && rrel >= 0 && rrel < 32) ? (1u << rrel) : 0u);
+          const int o = rprev + __popc(rmask & le_mask) - 1;
+          rprev += __popc(rmask);
+          // ---- 3. pixel span of each job's row: every edge function >= 0
+          int len = 0, xa = 0, Yr = 0;
+          if (rb + lane < rtotal) {
+            const float4* R = reinterpret_cast<const float4*>(recs + o * kRec);
             const float4 r0 = R[0];
-            const int w = __float_as_int(r0.z);
-            const int dy = (int)(((float)kk + 0.5f) * r0.w);
-            const int dx = kk - dy * w;
-            const int X = __float_as_int(r0.x) + dx, Y = __float_as_int(r0.y) + dy;
-            const float fx = (float)X, fy = (float)Y;
-            const float4 ra = R[1], rb = R[2], rc = R[3];
-            const float f0 = fmaf(ra.x, fx, fmaf(rb.x, fy, rc.x));
-            const float f1 = fmaf(ra.y, fx, fmaf(rb.y, fy, rc.y));
-            const float f2 = fmaf(ra.z, fx, fmaf(rb.z, fy, rc.z));
-            const float f3 = fmaf(ra.w, fx, fmaf(rb.w, fy, rc.w));
-            const float Tv = fmaxf(fminf(fminf(f0, f1), fminf(f2, f3)), 0.0f);
-            float v = Tv;
-            float4 r5;
-            if (persp) {
-              const float4 r4 = R[4];
-              r5 = R[5];
-              const float M = fmaxf(fmaf(r4.x, fx, fmaf(r4.y, fy, r4.z)), fmaf(r4.w, fx, fmaf(r5.x, fy, r5.y)));
-              v = __fdividef(Tv, M * fmaf(r5.z, Tv, M));
-            } else if (!COUNT) {
-              r5 = R[5];
+            Yr = __float_as_int(r0.y) + (rb + lane - __float_as_int(r0.w));
+            const float fy = (float)Yr;
+            const float4 ra = R[1], rbv = R[2], rc = R[3], ri = R[4];
+            float lo = __int_as_float(0xff800000), hi = __int_as_float(0x7f800000);
+            span_edge(ra.x, fmaf(rbv.x, fy, rc.x), ri.x, lo, hi);
+            span_edge(ra.y, fmaf(rbv.y, fy, rc.y), ri.y, lo, hi);
+            span_edge(ra.z, fmaf(rbv.z, fy, rc.z), ri.z, lo, hi);
+            span_edge(ra.w, fmaf(rbv.w, fy, rc.w), ri.w, lo, hi);
+            const float qx0f = (float)__float_as_int(r0.x), qx1f = (float)__float_as_int(r0.z);
+            lo = fmaxf(lo - 1e-3f, qx0f);
+            hi = fminf(hi + 1e-3f, qx1f);
+            if (lo <= hi) {
+              xa = (int)ceilf(lo);
+              len = max(0, (int)floorf(hi) - xa + 1);
             }
-            if (v > 0.0f) {
-              bool risky = false;
-              if (!COUNT && r5.w != 0.0f) {
-                // steepness of the edge that bounds the value here
-                const float4 r6 = R[6];
-                float sa = r6.x, mn = f0;
-                if (f1 < mn) { mn = f1; sa = r6.y; }
-                if (f2 < mn) { mn = f2; sa = r6.z; }
-                if (f3 < mn) { sa = r6.w; }
-                risky = sa * kErr * v > kTol * fmaxf(v, sig);
+          }
+          int ptotal;
+          const int poff = warp_excl_scan(len, ptotal);
+          const int jslot = __popc(__ballot_sync(FULL, len > 0) & lt_mask);
+          if (len > 0) jobs[jslot] = make_int4(xa, Yr, o, poff);
+          __syncwarp();
+          // ---- 4. walk the pixels of the jobs, 32 per step
+          int pprev = 0;
+          for (int pb = 0; pb < ptotal; pb += 32) {
+            const int prel = poff - pb;
+            const unsigned pmask = __reduce_or_sync(FULL, (len > 0 && prel >= 0 && prel < 32) ? (1u << prel) : 0u);
+            const int j = pprev + __popc(pmask & le_mask) - 1;
+            pprev += __popc(pmask);
+            if (pb + lane < ptotal) {
+              const int4 J = jobs[j];
+              const int X = J.x + (pb + lane - J.w), Y = J.y;
+              const float4* R = reinterpret_cast<const float4*>(recs + J.z * kRec);
+              const float fx = (float)X, fy = (float)Y;
+              const float4 ra = R[1], rbv = R[2], rc = R[3];
+              const float f0 = fmaf(ra.x, fx, fmaf(rbv.x, fy, rc.x));
+              const float f1 = fmaf(ra.y, fx, fmaf(rbv.y, fy, rc.y));
+              const float f2 = fmaf(ra.z, fx, fmaf(rbv.z, fy, rc.z));
+              const float f3 = fmaf(ra.w, fx, fmaf(rbv.w, fy, rc.w));
+              const float Tv = fmaxf(fminf(fminf(f0, f1), fminf(f2, f3)), 0.0f);
+              float v = Tv;
+              float4 r6;
+              if (persp) {
+                const float4 r5 = R[5];
+                r6 = R[6];
+                const float M =
+                    fmaxf(fmaf(r5.x, fx, fmaf(r5.y, fy, r5.z)), fmaf(r5.w, fx, fmaf(r6.x, fy, r6.y)));
+                v = __fdividef(Tv, M * fmaf(r6.z, Tv, M));
+              } else if (!COUNT) {
+                r6 = R[6];
               }
-              if (COUNT) {
-                ++nfrag;
-              } else if (!risky) {
-                accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], v, &a.ctr->errors);
-              } else {
-                const float4 r7 = R[7];
-                const int sxo = __float_as_int(r7.x), syo = __float_as_int(r7.y);
-                const unsigned slot = atomicAdd(&qn, 1u);
-                if (slot < (unsigned)kQueue) {
-                  queue[slot] = pack_frag((unsigned)(tb + owner), sxo, syo, X, Y);
+              if (v > 0.0f) {
+                if (COUNT) {
+                  ++nfrag;
                 } else {
-                  // queue full: keep the FP32 value (counted in the statistics)
-                  accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], v, &a.ctr->errors);
+                  bool risky = false;
+                  if (r6.w != 0.0f) {
+                    // steepness of the edge that bounds the value here
+                    const float4 r7 = R[7];
+                    float sa = r7.x, mn = f0;
+                    if (f1 < mn) { mn = f1; sa = r7.y; }
+                    if (f2 < mn) { mn = f2; sa = r7.z; }
+                    if (f3 < mn) { sa = r7.w; }
+                    risky = sa * kErr * v > kTol * fmaxf(v, sig);
+                  }
+                  if (!risky) {
+                    accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], v, &a.ctr->errors);
+                  } else {
+                    const float4 r8 = R[8];
+                    const unsigned qslot = atomicAdd(&qn, 1u);
+                    if (qslot < (unsigned)kQueue) {
+                      queue[qslot] = pack_frag((unsigned)(tb + __float_as_int(r8.z)), __float_as_int(r8.x), __float_as_int(r8.y), X, Y);
+                    } else {
+                      // queue full: keep the FP32 value (counted in the statistics)
+                      accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], v, &a.ctr->errors);
+                    }
+                  }
                 }
               }
             }
+            __syncwarp();
           }
-          carry = mask ? starts[31 - __clz(mask)] : carry;
-          __syncwarp();
         }
       }
       cr += step_r;
@@ -297,7 +355,7 @@ __global__ void __launch_bounds__(256, 2) k_tile(RasterArgs a, unsigned long lon
 
 static size_t tile_smem(int threads, int tile) {
   const int nw = threads / 32;
-  return sizeof(unsigned) * 2 * tile * tile + sizeof(float) * nw * 32 * kRec + sizeof(int) * nw * 32;
+  return sizeof(unsigned) * 2 * tile * tile + sizeof(float) * nw * 32 * kRec + sizeof(int4) * nw * 32;
 }
 
 int raster_max_ctas_per_sm(int threads, int tile, int any_persp) {
