@@ -322,3 +322,28 @@ def test_gradient_along_orthographic_axis_vanishes():
     g = oracle.gradient(pos, N, cam, rng.normal(size=(32, 32)))
     assert np.abs(g[:, :2]).max() > 1e-3
     assert np.abs(g[:, 2]).max() <= 1e-10 * np.abs(g[:, :2]).max()
+
+
+def test_local_difference_equals_full_render_difference():
+    """The incident-tetrahedra image swap used for central differences of
+    large frames reproduces differences of full oracle renders."""
+    from fd_local import incident_tets, local_image
+    N, W = 6, 48
+    pos = ZeldovichField.generate(N, -2.5, 2.5, 1005).positions(2.0)
+    tgt = ZeldovichField.generate(N, -2.5, 2.5, 2005).positions(2.0)
+    cam = ortho_z(W, W)
+    T = oracle.render(tgt, N, cam)
+    I = oracle.render(pos, N, cam)
+    pos64 = pos[:, :3].astype(np.float64)
+    h = 1e-5
+    for p in (0, N - 1, N ** 3 - 1, 77):
+        tets = incident_tets(p, N)
+        rest = I - local_image(pos64, N, tets, cam) - T
+        for ax in range(3):
+            pp = pos64.copy()
+            pp[p, ax] += h
+            up, Lp = local_image(pp, N, tets, cam), np.sum((oracle.render(pp, N, cam) - T) ** 2)
+            pp[p, ax] -= 2 * h
+            dn, Lm = local_image(pp, N, tets, cam), np.sum((oracle.render(pp, N, cam) - T) ** 2)
+            local = np.sum((up - dn) * (up + dn + 2.0 * rest))
+            assert local == pytest.approx(Lp - Lm, rel=1e-8, abs=1e-12 * max(1.0, abs(Lp)))
