@@ -230,6 +230,37 @@ lt_status lt_graph_launch(lt_ctx* ctx, lt_stream stream);
 lt_status lt_autotune(lt_ctx* ctx, const lt_camera* cams, int n_frames, const int* frame_snapshot,
                       float* d_image, int reps, lt_config* best, lt_stream stream);
 
+/*
+ * lt_frame_mass_static -- the per-frame mass of images the caller already
+ * holds: for each frame, the sum of its pixel values times pixel_area, in
+ * FP64 and in a fixed order (the reduction lt_render_tiles does for
+ * d_mass). The paper has no counterpart: it exists for callers that must
+ * not allocate device memory, for example one whose memory pool owns all
+ * free device memory, or one that must not hit the implicit device
+ * synchronisation an allocation or a free can cause. It allocates nothing
+ * and needs no context.
+ *
+ * d_image: float [n_frames][H][W] (caller owned, read only). d_mass: double
+ * [n_frames] (caller owned, overwritten). pixel_area > 0: one value for all
+ * frames (orthographic: window area / (W H); perspective: the image-plane
+ * pixel area at unit distance, as lt_render_tiles uses). Asynchronous on
+ * `stream`.
+ *
+ * Scratch: one static device array per GPU of 155,648 bytes (128 frames x
+ * 152 partial sums). It needs no initialisation: every partial is written
+ * before it is read. Because it is shared, calls that can run at the same
+ * time on one device (several streams or host threads) race on it and give
+ * wrong sums: order them (one stream, or events between streams).
+ * The first call on each device looks up the scratch address with that
+ * device current; make that first call before any stream capture begins.
+ *
+ * Errors: LT_ERR_ARG (null pointer, n_frames, W or H < 1, pixel_area not a
+ * positive finite number), LT_ERR_CAPACITY (n_frames > 128: split the
+ * frames over several calls), LT_ERR_CUDA (symbol lookup or launch failed).
+ */
+lt_status lt_frame_mass_static(const float* d_image, int n_frames, int W, int H, double pixel_area, double* d_mass,
+                               lt_stream stream);
+
 /* Wait for the stream, then return (and clear) the first latched device error. */
 lt_status lt_sync(lt_ctx* ctx, lt_stream stream);
 

@@ -70,7 +70,7 @@ STATUS = {
 EXPORTS = [
     "lt_create", "lt_destroy", "lt_set_config", "lt_get_config", "lt_build_tets", "lt_project_bin",
     "lt_render_tiles", "lt_render_atomic", "lt_count_fragments", "lt_render_backward", "lt_graph_build",
-    "lt_graph_launch", "lt_autotune", "lt_sync", "lt_get_stats", "lt_status_str",
+    "lt_graph_launch", "lt_autotune", "lt_sync", "lt_get_stats", "lt_status_str", "lt_frame_mass_static",
 ]
 
 
@@ -119,6 +119,7 @@ def load(build_if_missing: bool = False):
         "lt_sync": ([vp, vp], C.c_int),
         "lt_get_stats": ([vp, C.POINTER(LtStats)], C.c_int),
         "lt_status_str": ([C.c_int], C.c_char_p),
+        "lt_frame_mass_static": ([vp, C.c_int, C.c_int, C.c_int, C.c_double, vp, vp], C.c_int),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)

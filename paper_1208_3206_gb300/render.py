@@ -247,6 +247,25 @@ def lt_render_backward(r: Renderer, *a, **k):
     return r.render_backward(*a, **k)
 
 
+def lt_frame_mass_static(image: torch.Tensor, pixel_area: float, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Per-frame mass (sum of pixels times pixel_area, FP64, fixed order) of a
+    float32 CUDA image [F][H][W], through the library's allocation-free
+    entry point (no context; its scratch is static device memory, so calls
+    on one device must not overlap). `out`: float64 CUDA [F] (allocated here
+    when None, by the caller's PyTorch)."""
+    if image.dtype != torch.float32 or not image.is_cuda or not image.is_contiguous() or image.dim() != 3:
+        raise ValueError("image must be a contiguous float32 CUDA tensor [F][H][W]")
+    F, H, W = image.shape
+    if out is None:
+        out = torch.empty(F, dtype=torch.float64, device=image.device)
+    if out.dtype != torch.float64 or not out.is_cuda or out.numel() != F or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 CUDA tensor with one entry per frame")
+    lib = _lib.load()
+    check("lt_frame_mass_static", lib.lt_frame_mass_static(_ptr(image), int(F), int(W), int(H), float(pixel_area),
+                                                           _ptr(out), _stream()))
+    return out
+
+
 class LTRender(torch.autograd.Function):
     """image = LTRender.apply(pos, renderer, cams): forward through
     lt_build_tets + lt_project_bin + lt_render_tiles, backward through
