@@ -43,6 +43,8 @@ struct lt_ctx {
   unsigned long long* d_off = nullptr;
   unsigned long long* d_work = nullptr;
   double* d_mass_tile = nullptr;
+  unsigned long long* d_xq = nullptr;  // exact-evaluation queues of the raster CTAs
+  size_t xq_cap = 0;
   unsigned long long* d_scan_tmp = nullptr;
   size_t scan_tmp_cap = 0;
   unsigned* d_list = nullptr;
@@ -350,6 +352,8 @@ lt_status ensure_tiles(lt_ctx* ctx, long long n) {
   }
   const size_t words = lt::scan_tmp_words(n);
   if ((st = grow(&ctx->d_scan_tmp, &ctx->scan_tmp_cap, words)) != LT_OK) return st;
+  const size_t xq = (size_t)ctx->num_sms * lt::kRasterMaxCtasPerSm * lt::kExactQueueCap;
+  if ((st = grow(&ctx->d_xq, &ctx->xq_cap, xq)) != LT_OK) return st;
   return LT_OK;
 }
 
@@ -391,11 +395,14 @@ lt_status render_impl(lt_ctx* ctx, float* d_image, double* d_mass, cudaStream_t 
   a.mass_tile = ctx->d_mass_tile;
   a.ctr = ctx->d_ctr;
   a.tile = ctx->tile;
+  a.xq = ctx->d_xq;
+  a.xq_cap = lt::kExactQueueCap;
   const int threads = ctx->cfg.raster_threads;
   int cps = ctx->cfg.ctas_per_sm;
   const int fit = lt::raster_max_ctas_per_sm(threads, ctx->tile, ctx->any_persp);
   if (fit < 1) return LT_ERR_ARG;  // CTA shape exceeds the SM's registers or shared memory
   if (cps <= 0 || cps > fit) cps = fit;
+  if (cps > lt::kRasterMaxCtasPerSm) cps = lt::kRasterMaxCtasPerSm;  // the exact queues are sized for this
   long long ctas = (long long)ctx->num_sms * cps;
   if (ctas > ctx->n_tiles) ctas = ctx->n_tiles;
   if (ctas < 1) ctas = 1;
@@ -466,6 +473,7 @@ void lt_destroy(lt_ctx* ctx) {
   cudaFree(ctx->d_off);
   cudaFree(ctx->d_work);
   cudaFree(ctx->d_mass_tile);
+  cudaFree(ctx->d_xq);
   cudaFree(ctx->d_scan_tmp);
   cudaFree(ctx->d_list);
   cudaFree(ctx->d_hist);
@@ -568,6 +576,8 @@ lt_status lt_count_fragments(lt_ctx* ctx, long long* h_counts, lt_stream stream)
   a.mass_tile = nullptr;
   a.ctr = ctx->d_ctr;
   a.tile = ctx->tile;
+  a.xq = nullptr;  // counting queues nothing
+  a.xq_cap = 0;
   long long ctas = (long long)ctx->num_sms * 4;
   if (ctas > ctx->n_tiles) ctas = ctx->n_tiles;
   LT_CUDA(lt::launch_count_fragments(a, ctx->d_frag, ctx->n_frames, (int)ctas, 256, s));

@@ -150,11 +150,13 @@ __global__ void __launch_bounds__(128) k_backward(Lattice L, const FrameDev* __r
             }
           }
         }
-      // pixel -> world: x_pix = (r . P) sx + const, y_pix = (u . P) sy + const
+      // pixel -> world: x_pix = (r . P) sx + const, y_pix = (u . P) sy + const; the
+      // edge functions are in fixed-point accumulator units, converted by F.unit
+      const float unit = (float)F.unit;
 #pragma unroll
       for (int n = 0; n < 8; ++n)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) G[n][q] += gpx[n] * F.sx * F.r[q] + gpy[n] * F.sy * F.u[q];
+        for (int q = 0; q < 3; ++q) G[n][q] += (gpx[n] * F.sx * F.r[q] + gpy[n] * F.sy * F.u[q]) * unit;
     }
     float* out = corner_grad + ((long long)snap * ncube + cube) * 24;
 #pragma unroll

@@ -389,7 +389,8 @@ struct TetRaster {
   // steepness |e|^2 / min(|o1|, |o2|) of each edge (0 for unused slots): the
   // FP32 round-off of an edge's value grows in proportion to it
   float st[4];
-  float hmax;  // upper bound of the value over the tetrahedron (accumulator units)
+  float hmax;    // upper bound of the value over the tetrahedron (accumulator units)
+  float vscale;  // perspective: bound of d value / d T (1 / w_min^2); 1 orthographic
 };
 
 __device__ __forceinline__ float cross2(float ax, float ay, float bx, float by) { return ax * by - ay * bx; }
@@ -554,9 +555,11 @@ __device__ __forceinline__ bool tet_setup(float x0, float y0, float x1, float y1
   }
   // pyramid apex value 2 Kn / S; the perspective depth factor is at most 1 / w_min^2
   t.hmax = __fdividef(2.0f * Kn, K.S);
+  t.vscale = 1.0f;
   if (PERSP) {
     const float wmin = wa + fminf(fminf(w0, w1), fminf(w2, w3));
-    t.hmax = __fdividef(t.hmax, wmin * wmin);
+    t.vscale = __frcp_rn(wmin * wmin);
+    t.hmax = t.hmax * t.vscale;
   }
   if (PERSP) {
     const float* X = K.x;
@@ -741,18 +744,58 @@ __device__ __noinline__ static double exact_fragment(const Lattice& L, const Fra
   return half ? val / dl : val;
 }
 
-// A fragment's FP32 value carries a relative error of about kFragErr times
-// the steepness of its active pyramid edge; it is recomputed exactly when
-// that error could exceed kFragTol of max(value, mean column density).
+// Error model of a fragment's FP32 value (accumulator units), with e its
+// active pyramid edge (the smallest edge function):
+//   * the round-off of the edge function itself, relative, about kFragErr
+//     times the edge's steepness |e|^2 / min(|o1|, |o2|);
+//   * the rounding of the projected vertex positions, absolute: the edge
+//     moves by up to delta pixels, changing the value by up to its slope
+//     (|a_e| + |b_e|) times delta. Thin projected slivers have huge slopes.
+// In perspective both are scaled by d value / d T = 1 / (M + g T)^2.
+// A fragment is recomputed exactly when the bound could exceed kFragTol of
+// max(value, mean column density); so is a pixel just outside the FP32 hull
+// that the vertex uncertainty could move inside.
 constexpr float kFragErr = 1e-5f;
 constexpr float kFragTol = 1e-5f;
 
-// True when some fragment of a set-up tetrahedron may need the exact path:
-// its steepest edge's round-off bound could pass kFragTol of
-// max(value, mean column density) somewhere.
-__device__ __forceinline__ bool may_need_exact(const TetRaster& t, float sigma_units) {
+// Vertex position uncertainty (pixels) of a tetrahedron whose vertices lie
+// within R pixels of its cube's anchor (R includes, in perspective, the
+// depth terms of the projection): about four ulp of R from the displacement
+// and projection arithmetic, plus the tile-relative subtraction.
+__device__ __forceinline__ float vertex_uncertainty(float R) {
+  return R * (1.0f / 2097152.0f) + (1.0f / 524288.0f);  // 2^-21 R + 2^-19
+}
+
+__device__ __forceinline__ float max_edge_slope(const TetRaster& t) {
+  return fmaxf(fmaxf(fabsf(t.a[0]) + fabsf(t.b[0]), fabsf(t.a[1]) + fabsf(t.b[1])),
+               fmaxf(fabsf(t.a[2]) + fabsf(t.b[2]), fabsf(t.a[3]) + fabsf(t.b[3])));
+}
+
+// True when some fragment of a set-up tetrahedron may need the exact path.
+__device__ __forceinline__ bool may_need_exact(const TetRaster& t, float sigma_units, float delta) {
   const float stmax = fmaxf(fmaxf(t.st[0], t.st[1]), fmaxf(t.st[2], t.st[3]));
-  return stmax * kFragErr * t.hmax > kFragTol * fminf(t.hmax, sigma_units);
+  return max_edge_slope(t) * delta * t.vscale + stmax * kFragErr * t.hmax > kFragTol * fminf(t.hmax, sigma_units);
+}
+
+// True when the vertex uncertainty could move a pixel whose value matters
+// across the FP32 hull boundary (steep thin slivers): such a tetrahedron has
+// its whole bounding box visited.
+__device__ __forceinline__ bool may_miss_fragments(const TetRaster& t, float sigma_units, float delta) {
+  return max_edge_slope(t) * delta * t.vscale > kFragTol * sigma_units;
+}
+
+// Exact-path decision for one candidate pixel of a flagged tetrahedron: f the
+// four edge functions there, a, b, st their gradients and steepness, dvdT
+// the perspective factor (1 orthographic), v the FP32 value.
+__device__ __forceinline__ bool fragment_needs_exact(float f0, float f1, float f2, float f3, float4 a, float4 b,
+                                                     float4 st, float delta, float dvdT, float v, float sigma_units) {
+  float mn = f0, ae = a.x, be = b.x, se = st.x;
+  if (f1 < mn) { mn = f1; ae = a.y; be = b.y; se = st.y; }
+  if (f2 < mn) { mn = f2; ae = a.z; be = b.z; se = st.z; }
+  if (f3 < mn) { mn = f3; ae = a.w; be = b.w; se = st.w; }
+  const float pos_err = (fabsf(ae) + fabsf(be)) * delta;
+  if (!(mn > 0.0f)) return mn > -pos_err && pos_err * dvdT > kFragTol * sigma_units;
+  return (pos_err + kFragErr * se * mn) * dvdT > kFragTol * fmaxf(v, sigma_units);
 }
 
 // Number of periodic copies: shift range s in [s0, s1] such that the span

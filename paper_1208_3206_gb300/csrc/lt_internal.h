@@ -37,9 +37,13 @@ struct RasterArgs {
   double* mass_tile;       // per global tile
   DevCounters* ctr;
   int tile;
+  unsigned long long* xq;  // exact-evaluation queue, xq_cap entries per CTA
+  unsigned xq_cap;
 };
 cudaError_t launch_raster(const RasterArgs& a, int ctas, int threads, int any_persp, cudaStream_t s);
 int raster_max_ctas_per_sm(int threads, int tile, int any_persp);
+constexpr int kRasterMaxCtasPerSm = 4;     // CTAs per SM the exact queue is sized for
+constexpr unsigned kExactQueueCap = 32768;  // queued fragments per CTA and tile
 cudaError_t launch_count_fragments(const RasterArgs& a, unsigned long long* d_counts, int n_frames, int ctas,
                                    int threads, cudaStream_t s);
 cudaError_t launch_mass_reduce(const double* mass_tile, long long tpf, int n_frames, double* d_mass,

@@ -32,8 +32,15 @@ __device__ __forceinline__ void cube_fragments(const CubeProj& P, const FrameDev
         const float txmax = fmaxf(fmaxf(P.x[c0], P.x[c1]), fmaxf(P.x[c2], P.x[c3]));
         const float tymin = fminf(fminf(P.y[c0], P.y[c1]), fminf(P.y[c2], P.y[c3]));
         const float tymax = fmaxf(fmaxf(P.y[c0], P.y[c1]), fmaxf(P.y[c2], P.y[c3]));
-        const int qx0 = max(px0, (int)ceilf(ax + txmin - 1e-3f)), qx1 = min(px1, (int)floorf(ax + txmax + 1e-3f));
-        const int qy0 = max(py0, (int)ceilf(ay + tymin - 1e-3f)), qy1 = min(py1, (int)floorf(ay + tymax + 1e-3f));
+        float Rv = fmaxf(fmaxf(fabsf(txmin), fabsf(txmax)), fmaxf(fabsf(tymin), fabsf(tymax)));
+        if (PERSP) {
+          const float dwm = fmaxf(fmaxf(fabsf(P.dw[c0]), fabsf(P.dw[c1])), fmaxf(fabsf(P.dw[c2]), fabsf(P.dw[c3])));
+          Rv += fmaxf(fabsf(P.axh - F.cx), fabsf(P.ayh - F.cy)) * __fdividef(dwm, P.w0);
+        }
+        const float delta = vertex_uncertainty(Rv);
+        const float mg = 1e-3f + delta;
+        const int qx0 = max(px0, (int)ceilf(ax + txmin - mg)), qx1 = min(px1, (int)floorf(ax + txmax + mg));
+        const int qy0 = max(py0, (int)ceilf(ay + tymin - mg)), qy1 = min(py1, (int)floorf(ay + tymax + mg));
         if (qx0 > qx1 || qy0 > qy1) continue;
         float Kn = 6.0f * F.K, invKn = 0.0f;
         if (PERSP) {
@@ -57,29 +64,34 @@ __device__ __forceinline__ void cube_fragments(const CubeProj& P, const FrameDev
           }
           float lo, hi;
           row_span(t, erow, lo, hi);
-          const int xa = max(qx0, (int)ceilf(fmaxf(lo + ax, -1.0e9f)));
-          const int xb = min(qx1, (int)floorf(fminf(hi + ax, 1.0e9f)));
-          const bool check = EXACT && may_need_exact(t, F.sigma_units);
+          const bool check = EXACT && may_need_exact(t, F.sigma_units, delta);
+          // a steep sliver visits its whole bounding-box row: pixels the
+          // vertex uncertainty could move inside are checked too
+          const bool whole = EXACT && may_miss_fragments(t, F.sigma_units, delta);
+          const int xa = whole ? qx0 : max(qx0, (int)ceilf(fmaxf(lo + ax, -1.0e9f)));
+          const int xb = whole ? qx1 : min(qx1, (int)floorf(fminf(hi + ax, 1.0e9f)));
           for (int px = xa; px <= xb; ++px) {
             const float X = rel_coord(px, shx, P.axh, P.axl);
-            const float v = tet_value<PERSP>(t, X, erow, prow);
-            if (!(v > 0.0f)) continue;
-            if (check) {
-              // same ill-conditioning test as the tile raster: the steepness of the
-              // active edge bounds the FP32 round-off of this value
-              float sa = t.st[0], mn = fmaf(t.a[0], X, erow[0]);
-#pragma unroll
-              for (int e = 1; e < 4; ++e) {
-                const float fe = fmaf(t.a[e], X, erow[e]);
-                if (fe < mn) { mn = fe; sa = t.st[e]; }
-              }
-              if (sa * kFragErr * v > kFragTol * fmaxf(v, F.sigma_units)) {
-                const double ex = exact_fragment(Lat, F, cube, s, sx, sy, px, py, F.m_tet);
-                fn(px, py, (float)(ex / F.unit));
-                continue;
-              }
+            const float f0 = fmaf(t.a[0], X, erow[0]), f1 = fmaf(t.a[1], X, erow[1]);
+            const float f2 = fmaf(t.a[2], X, erow[2]), f3 = fmaf(t.a[3], X, erow[3]);
+            const float T = fmaxf(fminf(fminf(f0, f1), fminf(f2, f3)), 0.0f);
+            float v = T, dvdT = 1.0f;
+            if (PERSP) {
+              const float M = fmaxf(fmaf(t.pa[0], X, prow[0]), fmaf(t.pa[1], X, prow[1]));
+              const float den = M * fmaf(t.g, T, M);
+              v = __fdividef(T, den);
+              const float q = __fdividef(M, den);
+              dvdT = q * q;
             }
-            fn(px, py, v);
+            if (check && fragment_needs_exact(f0, f1, f2, f3, make_float4(t.a[0], t.a[1], t.a[2], t.a[3]),
+                                              make_float4(t.b[0], t.b[1], t.b[2], t.b[3]),
+                                              make_float4(t.st[0], t.st[1], t.st[2], t.st[3]), delta, dvdT, v,
+                                              F.sigma_units)) {
+              const double ex = exact_fragment(Lat, F, cube, s, sx, sy, px, py, F.m_tet);
+              if (ex > 0.0) fn(px, py, (float)(ex / F.unit));
+              continue;
+            }
+            if (v > 0.0f) fn(px, py, v);
           }
         }
       }

@@ -23,16 +23,16 @@
 namespace lt {
 
 constexpr int kRec = 36;  // words per tetrahedron record (stride 4 mod 32: float4 access is conflict-free)
-constexpr int kQueue = 2048;  // ill-conditioned fragments queued per tile
+// Ill-conditioned fragments are queued per CTA in global memory (a.xq_cap
+// entries per CTA) and evaluated exactly after the tile's walk.
 
 // Record layout, in float4 groups so the walk reads it with a few 128-bit
-// loads: [0] qx0, qy0, qx1 (bounding box in tile pixels); [1] a[4]; [2] b[4];
-// [3] c[4] (edge functions); [4] 1/a[4] (row spans); [5] pa0, pb0, pc0, pa1;
-// [6] pb1, pc1, g (perspective depth planes), exact-check flag; [7] edge
-// steepness st[4]; [8] periodic copy (sx, sy).
+// loads: [0] qx0, qy0, qx1 | flag << 16 (bounding box in tile pixels),
+// first row job; [1] a[4]; [2] b[4]; [3] c[4] (edge functions); [4] 1/a[4]
+// (row spans); [5] pa0, pb0, pc0, pa1; [6] pb1, pc1, g (perspective depth
+// planes), exact-check flag; [7] edge steepness st[4]; [8] periodic copy
+// (sx, sy), lane, vertex uncertainty.
 
-constexpr float kErr = kFragErr;
-constexpr float kTol = kFragTol;
 
 __device__ __forceinline__ unsigned long long pack_frag(unsigned tau, int sx, int sy, int X, int Y) {
   return (unsigned long long)tau | ((unsigned long long)(unsigned)(sx + 64) << 32) |
@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
   int4* jobs = reinterpret_cast<int4*>(reinterpret_cast<float*>(acc_hi + T * T) + nw * 32 * kRec) + warp * 32;
   __shared__ unsigned long long item_s;
   __shared__ double mass_w[32];
-  __shared__ unsigned long long queue[kQueue];
   __shared__ unsigned qn;
+  unsigned long long* xq = a.xq + (size_t)blockIdx.x * a.xq_cap;
   const unsigned FULL = 0xffffffffu;
   unsigned long long nfrag = 0;
 
@@ -141,6 +141,20 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
         sy1 = min(sy1, sy0 + 63);
       }
       const int ncx = max(0, sx1 - sx0 + 1), ncp = ncx * max(0, sy1 - sy0 + 1);
+      float delta = 0.f;
+      if (ok) {
+        const float Rx = fmaxf(fmaxf(fabsf(P.x[0]), fabsf(P.x[1])), fmaxf(fabsf(P.x[2]), fabsf(P.x[3])));
+        const float Ry = fmaxf(fmaxf(fabsf(P.y[0]), fabsf(P.y[1])), fmaxf(fabsf(P.y[2]), fabsf(P.y[3])));
+        float Rv = fmaxf(Rx, Ry);
+        if (persp) {
+          // the anchor's offset from the view axis times the depth offsets
+          const float dwm = fmaxf(fmaxf(fabsf(P.dw[0]), fabsf(P.dw[1])), fmaxf(fabsf(P.dw[2]), fabsf(P.dw[3])));
+          const float off = fmaxf(fabsf(P.axh - F.cx), fabsf(P.ayh - F.cy));
+          Rv += off * __fdividef(dwm, P.w0);
+        }
+        delta = vertex_uncertainty(Rv);
+      }
+      const float margin = 1e-3f + delta;
       const int rounds = __reduce_max_sync(FULL, ncp);
       float Kn = Kn0, invKn = 0.f;
       if (persp && ok) {
@@ -158,10 +172,10 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
           const float oy = ((float)(ty0 - sy * F.H) - P.ayh) - P.ayl;
           const float x0 = P.x[0] - ox, x1 = P.x[1] - ox, x2 = P.x[2] - ox, x3 = P.x[3] - ox;
           const float y0 = P.y[0] - oy, y1 = P.y[1] - oy, y2 = P.y[2] - oy, y3 = P.y[3] - oy;
-          qx0 = max(0, (int)ceilf(bx0 - ox - 1e-3f));
-          qx1 = min(tw - 1, (int)floorf(bx1 - ox + 1e-3f));
-          qy0 = max(0, (int)ceilf(by0 - oy - 1e-3f));
-          const int qy1 = min(th - 1, (int)floorf(by1 - oy + 1e-3f));
+          qx0 = max(0, (int)ceilf(bx0 - ox - margin));
+          qx1 = min(tw - 1, (int)floorf(bx1 - ox + margin));
+          qy0 = max(0, (int)ceilf(by0 - oy - margin));
+          const int qy1 = min(th - 1, (int)floorf(by1 - oy + margin));
           if (qx0 <= qx1 && qy0 <= qy1) {
             const bool set =
                 persp ? tet_setup<true>(x0, y0, x1, y1, x2, y2, x3, y3, P.dw[0], P.dw[1], P.dw[2], P.dw[3], Kn,
@@ -178,12 +192,15 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
         const int roff = warp_excl_scan(nrows, rtotal);
         if (nrows > 0) {
           float4* R = reinterpret_cast<float4*>(recs + slot * kRec);
-          R[0] = make_float4(__int_as_float(qx0), __int_as_float(qy0), __int_as_float(qx1), __int_as_float(roff));
+          const bool flagged = may_need_exact(t, sig, delta);
+          const bool whole_rows = may_miss_fragments(t, sig, delta);
+          R[0] = make_float4(__int_as_float(qx0), __int_as_float(qy0), __int_as_float(qx1 | (whole_rows ? 0x10000 : 0)),
+                             __int_as_float(roff));
           R[1] = make_float4(t.a[0], t.a[1], t.a[2], t.a[3]);
           R[2] = make_float4(t.b[0], t.b[1], t.b[2], t.b[3]);
           R[3] = make_float4(t.c[0], t.c[1], t.c[2], t.c[3]);
           R[4] = make_float4(inv_or_zero(t.a[0]), inv_or_zero(t.a[1]), inv_or_zero(t.a[2]), inv_or_zero(t.a[3]));
-          const float flag = may_need_exact(t, sig) ? 1.0f : 0.0f;
+          const float flag = flagged ? 1.0f : 0.0f;
           if (persp) {
             R[5] = make_float4(t.pa[0], t.pb[0], t.pc[0], t.pa[1]);
             R[6] = make_float4(t.pb[1], t.pc[1], t.g, flag);
@@ -191,7 +208,7 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
             R[6] = make_float4(0.f, 0.f, 0.f, flag);
           }
           R[7] = make_float4(t.st[0], t.st[1], t.st[2], t.st[3]);
-          R[8] = make_float4(__int_as_float(sx), __int_as_float(sy), __int_as_float(lane), 0.f);
+          R[8] = make_float4(__int_as_float(sx), __int_as_float(sy), __int_as_float(lane), delta);
         }
         __syncwarp();
         // The owner of a position in a 32-wide step is the last run starting
@@ -217,7 +234,14 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
             span_edge(ra.y, fmaf(rbv.y, fy, rc.y), ri.y, lo, hi);
             span_edge(ra.z, fmaf(rbv.z, fy, rc.z), ri.z, lo, hi);
             span_edge(ra.w, fmaf(rbv.w, fy, rc.w), ri.w, lo, hi);
-            const float qx0f = (float)__float_as_int(r0.x), qx1f = (float)__float_as_int(r0.z);
+            const int qx1w = __float_as_int(r0.z);
+            const float qx0f = (float)__float_as_int(r0.x), qx1f = (float)(qx1w & 0xffff);
+            if (qx1w >> 16) {
+              // a steep sliver: the whole bounding-box row, so that pixels the
+              // vertex uncertainty could move inside are checked too
+              lo = qx0f;
+              hi = qx1f;
+            }
             lo = fmaxf(lo - 1e-3f, qx0f);
             hi = fminf(hi + 1e-3f, qx1f);
             if (lo <= hi) {
@@ -237,6 +261,10 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
             const unsigned pmask = __reduce_or_sync(FULL, (len > 0 && prel >= 0 && prel < 32) ? (1u << prel) : 0u);
             const int j = pprev + __popc(pmask & le_mask) - 1;
             pprev += __popc(pmask);
+            bool exact = false;
+            unsigned long long qent = 0;
+            float vq = 0.f;
+            int Xq = 0, Yq = 0;
             if (pb + lane < ptotal) {
               const int4 J = jobs[j];
               const int X = J.x + (pb + lane - J.w), Y = J.y;
@@ -249,41 +277,53 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
               const float f3 = fmaf(ra.w, fx, fmaf(rbv.w, fy, rc.w));
               const float Tv = fmaxf(fminf(fminf(f0, f1), fminf(f2, f3)), 0.0f);
               float v = Tv;
-              float4 r6;
+              float4 r6 = make_float4(0.f, 0.f, 0.f, 0.f);
+              float dvdT = 1.0f;
               if (persp) {
                 const float4 r5 = R[5];
                 r6 = R[6];
                 const float M =
                     fmaxf(fmaf(r5.x, fx, fmaf(r5.y, fy, r5.z)), fmaf(r5.w, fx, fmaf(r6.x, fy, r6.y)));
-                v = __fdividef(Tv, M * fmaf(r6.z, Tv, M));
+                const float den = M * fmaf(r6.z, Tv, M);
+                v = __fdividef(Tv, den);
+                const float q = __fdividef(M, den);
+                dvdT = q * q;
               } else if (!COUNT) {
                 r6 = R[6];
               }
-              if (v > 0.0f) {
-                if (COUNT) {
-                  ++nfrag;
+              if (COUNT) {
+                if (v > 0.0f) ++nfrag;
+              } else if (v > 0.0f || r6.w != 0.0f) {
+                // flagged tetrahedra: fragments whose error bound is too large,
+                // and pixels the vertex uncertainty could move inside, go to
+                // the exact evaluation
+                exact = r6.w != 0.0f && fragment_needs_exact(f0, f1, f2, f3, ra, rbv, R[7], R[8].w, dvdT, v, sig);
+                if (!exact) {
+                  if (v > 0.0f) accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], v, &a.ctr->errors);
                 } else {
-                  bool risky = false;
-                  if (r6.w != 0.0f) {
-                    // steepness of the edge that bounds the value here
-                    const float4 r7 = R[7];
-                    float sa = r7.x, mn = f0;
-                    if (f1 < mn) { mn = f1; sa = r7.y; }
-                    if (f2 < mn) { mn = f2; sa = r7.z; }
-                    if (f3 < mn) { sa = r7.w; }
-                    risky = sa * kErr * v > kTol * fmaxf(v, sig);
-                  }
-                  if (!risky) {
-                    accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], v, &a.ctr->errors);
-                  } else {
-                    const float4 r8 = R[8];
-                    const unsigned qslot = atomicAdd(&qn, 1u);
-                    if (qslot < (unsigned)kQueue) {
-                      queue[qslot] = pack_frag((unsigned)(tb + __float_as_int(r8.z)), __float_as_int(r8.x), __float_as_int(r8.y), X, Y);
-                    } else {
-                      // queue full: keep the FP32 value (counted in the statistics)
-                      accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], v, &a.ctr->errors);
-                    }
+                  const float4 r8 = R[8];
+                  qent = pack_frag((unsigned)(tb + __float_as_int(r8.z)), __float_as_int(r8.x), __float_as_int(r8.y),
+                                   X, Y);
+                  vq = v;
+                  Xq = X;
+                  Yq = Y;
+                }
+              }
+            }
+            if (!COUNT) {
+              const unsigned em = __ballot_sync(FULL, exact);
+              if (em) {
+                const int leader = __ffs(em) - 1;
+                unsigned base = 0;
+                if (lane == leader) base = atomicAdd(&qn, (unsigned)__popc(em));
+                base = __shfl_sync(FULL, base, leader);
+                if (exact) {
+                  const unsigned slot = base + __popc(em & lt_mask);
+                  if (slot < a.xq_cap) {
+                    xq[slot] = qent;
+                  } else if (vq > 0.0f) {
+                    // queue full: keep the FP32 value (counted in the statistics)
+                    accum_fixed(&acc_lo[Yq * T + Xq], &acc_hi[Yq * T + Xq], vq, &a.ctr->errors);
                   }
                 }
               }
@@ -307,13 +347,13 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
     }
     __syncthreads();
     // ---- ill-conditioned fragments: exact FP64 evaluation, all lanes busy
-    const unsigned nq = min(qn, (unsigned)kQueue);
+    const unsigned nq = min(qn, a.xq_cap);
     if (threadIdx.x == 0 && qn) {
       atomicAdd(&a.ctr->exact_fragments, (unsigned long long)nq);
-      if (qn > (unsigned)kQueue) atomicAdd(&a.ctr->queue_overflow, (unsigned long long)(qn - kQueue));
+      if (qn > a.xq_cap) atomicAdd(&a.ctr->queue_overflow, (unsigned long long)(qn - a.xq_cap));
     }
     for (unsigned qi = threadIdx.x; qi < nq; qi += blockDim.x) {
-      const unsigned long long q = queue[qi];
+      const unsigned long long q = xq[qi];
       const unsigned tau_o = (unsigned)(q & 0xffffffffull);
       const int sxo = (int)((q >> 32) & 127u) - 64, syo = (int)((q >> 39) & 127u) - 64;
       const int X = (int)((q >> 46) & 63u), Y = (int)((q >> 52) & 63u);
