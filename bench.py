@@ -287,9 +287,7 @@ def run_lt(args, rank: int, world: int):
 
     # max over ranks
     if world > 1:
-        t = torch.tensor([ms, e2e_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+        ms, e2e_ms = max_over_ranks([ms, e2e_ms], dev)
 
     import torch.cuda as tc
     props = tc.get_device_properties(dev)
@@ -381,10 +379,21 @@ def cpu_baseline(c, pos_np, cams, snaps, crop: int):
                       f"{6 * c['N'] ** 3} tetrahedra)"}
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of a list of floats over all ranks of the
+    default process group (the slowest rank's times)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def run_reference(args, rank: int, world: int):
-    c, pos_np, cams, snaps = make_workload(args.workload, args.frames)
     if rank != 0:
-        return None
+        return None  # the CPU oracle runs on rank 0 only
+    c, pos_np, cams, snaps = make_workload(args.workload, args.frames)
     # each step: one bounded sample of the same workload (a central crop of
     # one frame), rotating through the frames
     for w in range(args.warmup):
@@ -412,21 +421,22 @@ def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        # rank 0 alone times the oracle; the other ranks exit without work
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
     if world > 1:
         import torch
         import torch.distributed as dist
 
-        backend = "nccl" if args.impl == "lt" else "gloo"
-        if args.impl == "lt":
-            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        dist.init_process_group(backend=backend)
-    if args.impl == "reference":
-        line = run_reference(args, rank, world)
-    else:
-        line, wl = run_lt(args, rank, world)
-        if rank == 0 and not args.no_cpu_baseline:
-            log("CPU oracle sample")
-            line["cpu_baseline"] = cpu_baseline(*wl, crop=args.cpu_sample_crop)
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend="nccl")
+    line, wl = run_lt(args, rank, world)
+    if rank == 0 and not args.no_cpu_baseline:
+        log("CPU oracle sample")
+        line["cpu_baseline"] = cpu_baseline(*wl, crop=args.cpu_sample_crop)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -278,16 +278,13 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
               const float Tv = fmaxf(fminf(fminf(f0, f1), fminf(f2, f3)), 0.0f);
               float v = Tv;
               float4 r6 = make_float4(0.f, 0.f, 0.f, 0.f);
-              float dvdT = 1.0f;
+              float M = 1.0f, den = 1.0f;
               if (persp) {
                 const float4 r5 = R[5];
                 r6 = R[6];
-                const float M =
-                    fmaxf(fmaf(r5.x, fx, fmaf(r5.y, fy, r5.z)), fmaf(r5.w, fx, fmaf(r6.x, fy, r6.y)));
-                const float den = M * fmaf(r6.z, Tv, M);
+                M = fmaxf(fmaf(r5.x, fx, fmaf(r5.y, fy, r5.z)), fmaf(r5.w, fx, fmaf(r6.x, fy, r6.y)));
+                den = M * fmaf(r6.z, Tv, M);
                 v = __fdividef(Tv, den);
-                const float q = __fdividef(M, den);
-                dvdT = q * q;
               } else if (!COUNT) {
                 r6 = R[6];
               }
@@ -297,7 +294,10 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
                 // flagged tetrahedra: fragments whose error bound is too large,
                 // and pixels the vertex uncertainty could move inside, go to
                 // the exact evaluation
-                exact = r6.w != 0.0f && fragment_needs_exact(f0, f1, f2, f3, ra, rbv, R[7], R[8].w, dvdT, v, sig);
+                if (r6.w != 0.0f) {
+                  const float q = persp ? __fdividef(M, den) : 1.0f;  // d value / d T = (M / den)^2
+                  exact = fragment_needs_exact(f0, f1, f2, f3, ra, rbv, R[7], R[8].w, q * q, v, sig);
+                }
                 if (!exact) {
                   if (v > 0.0f) accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], v, &a.ctr->errors);
                 } else {
