@@ -58,6 +58,9 @@ struct lt_ctx {
   unsigned long long* d_frag = nullptr;
   size_t frag_cap = 0;
   unsigned long long* h_u64 = nullptr;  // pinned scratch
+  // zero-volume tetrahedra: one bit per tetrahedron, a byte per (snapshot, cube)
+  unsigned char* d_degen = nullptr;
+  size_t degen_cap = 0;
   // backward
   float* d_corner_grad = nullptr;
   size_t corner_grad_cap = 0;
@@ -480,6 +483,7 @@ void lt_destroy(lt_ctx* ctx) {
   cudaFree(ctx->d_ctr);
   cudaFree(ctx->d_frag);
   cudaFree(ctx->d_corner_grad);
+  cudaFree(ctx->d_degen);
   if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
   if (ctx->h_u64) cudaFreeHost(ctx->h_u64);
   if (ctx->h_frames) cudaFreeHost(ctx->h_frames);
@@ -517,6 +521,9 @@ lt_status lt_build_tets(lt_ctx* ctx, const void* d_pos, int pos_fmt, int N, floa
   L.half_box = 0.5f * box;
   L.n_particles = (long long)N * N * N;
   lt::lattice_set_divisor(L, N);
+  lt_status st = grow(&ctx->d_degen, &ctx->degen_cap, (size_t)L.n_particles * n_snapshots);
+  if (st != LT_OK) return st;
+  L.degen = ctx->d_degen;
   ctx->L = L;
   ctx->n_snap = n_snapshots;
   ctx->total_mass = total_mass;
@@ -524,7 +531,7 @@ lt_status lt_build_tets(lt_ctx* ctx, const void* d_pos, int pos_fmt, int N, floa
   ctx->binned = false;
   LT_CUDA(cudaMemsetAsync(&ctx->d_ctr->nonfinite, 0, sizeof(unsigned long long) * 5, s));
   const double m = total_mass / (6.0 * (double)N * N * N);
-  LT_CUDA(lt::launch_build_tets(L, n_snapshots, m, d_rho, ctx->d_ctr, s));
+  LT_CUDA(lt::launch_build_tets(L, n_snapshots, m, d_rho, ctx->d_degen, ctx->d_ctr, s));
   return LT_OK;
 }
 

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(128) k_backward(Lattice L, const FrameDev* __r
           const float ax = axa + (float)shx, ay = aya + (float)shy;
 #pragma unroll
           for (int s = 0; s < 6; ++s) {
+            if (tet_degenerate(L, snap, cube, s)) continue;  // zero volume: contributes nothing
             const int c0 = tet_corner(s, 0), c1 = tet_corner(s, 1), c2 = tet_corner(s, 2), c3 = tet_corner(s, 3);
             TetRaster t;
             if (!tet_setup<false>(P.x[c0], P.y[c0], P.x[c1], P.y[c1], P.x[c2], P.y[c2], P.x[c3], P.y[c3], 0.f, 0.f,

@@ -13,7 +13,7 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned v
 }
 
 __global__ void __launch_bounds__(256) k_build_tets(Lattice L, int n_snap, double m, float* __restrict__ rho_out,
-                                                     DevCounters* __restrict__ ctr) {
+                                                     unsigned char* __restrict__ degen, DevCounters* __restrict__ ctr) {
   const long long ncube = L.n_particles;
   const long long total = ncube * n_snap;
   // FP32 determinant error is about 3 * 2^-24 * |e|^3 / |V| relative; below
@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(256) k_build_tets(Lattice L, int n_snap, doubl
         return dd;
       };
       n_nonfinite = ok0 ? 0u : 1u;  // each particle is corner 0 of exactly one cube
+      unsigned zero_mask = 0;
 #pragma unroll
       for (int s = 0; s < 6; ++s) {
         const int n0 = tet_corner(s, 0), n1 = tet_corner(s, 1), n2 = tet_corner(s, 2), n3 = tet_corner(s, 3);
@@ -80,13 +81,17 @@ __global__ void __launch_bounds__(256) k_build_tets(Lattice L, int n_snap, doubl
           Vd = (eax * (eby * ecz - ebz * ecy) + eay * (ebz * ecx - ebx * ecz) + eaz * (ebx * ecy - eby * ecx)) / 6.0;
           ++n_fb;
         }
-        if (Vd == 0.0) ++n_degen;
+        if (Vd == 0.0) {
+          ++n_degen;
+          zero_mask |= 1u << s;
+        }
         if (Vd > 0.0) ++n_inv;
         if (rho_out) {
           const float rho = (Vd == 0.0 || !(ok && ok0)) ? 0.0f : (float)(m / fabs(Vd));
           rho_out[(long long)snap * 6 * ncube + 6 * cube + s] = rho;
         }
       }
+      degen[gid] = (unsigned char)zero_mask;
     }
     warp_add_u64(&ctr->nonfinite, n_nonfinite);
     warp_add_u64(&ctr->degenerate, n_degen);
@@ -96,13 +101,13 @@ __global__ void __launch_bounds__(256) k_build_tets(Lattice L, int n_snap, doubl
   }
 }
 
-cudaError_t launch_build_tets(const Lattice& L, int n_snap, double m, float* rho_out, DevCounters* ctr,
-                              cudaStream_t s) {
+cudaError_t launch_build_tets(const Lattice& L, int n_snap, double m, float* rho_out, unsigned char* degen,
+                              DevCounters* ctr, cudaStream_t s) {
   const long long total = L.n_particles * n_snap;
   long long blocks = (total + 255) / 256;
   if (blocks > 152LL * 64) blocks = 152LL * 64;
   if (blocks < 1) blocks = 1;
-  k_build_tets<<<(unsigned)blocks, 256, 0, s>>>(L, n_snap, m, rho_out, ctr);
+  k_build_tets<<<(unsigned)blocks, 256, 0, s>>>(L, n_snap, m, rho_out, degen, ctr);
   return cudaGetLastError();
 }
 

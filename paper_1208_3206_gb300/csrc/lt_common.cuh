@@ -76,6 +76,9 @@ struct Lattice {
   int N;
   float box, h, half_box;
   long long n_particles;  // N^3 (< 2^31)
+  // per (snapshot, cube): bit s set when tetrahedron s has zero volume (such
+  // a tetrahedron contributes nothing; written by the build pass)
+  const unsigned char* degen;
   // unsigned division by N as a multiply-high and two shifts (Granlund and
   // Montgomery, "Division by invariant integers using multiplication", 1994,
   // Fig. 4.1): q = (t + ((n - t) >> s1)) >> s2, t = umulhi(div_m, n)
@@ -96,6 +99,11 @@ inline void lattice_set_divisor(Lattice& L, int N) {
 __device__ __forceinline__ unsigned div_n(const Lattice& L, unsigned n) {
   const unsigned t = __umulhi(L.div_m, n);
   return (t + ((n - t) >> L.div_s1)) >> L.div_s2;
+}
+
+// True when tetrahedron s of `cube` in snapshot `snap` has zero volume.
+__device__ __forceinline__ bool tet_degenerate(const Lattice& L, int snap, long long cube, int s) {
+  return L.degen && ((__ldg(L.degen + (long long)snap * L.n_particles + cube) >> s) & 1u);
 }
 
 // Lattice indices of a cube (= of its corner-0 particle) from its id.

@@ -9,8 +9,8 @@
 namespace lt {
 
 // ---- lt_build.cu: volumes, densities and position checks of every tetrahedron.
-cudaError_t launch_build_tets(const Lattice& L, int n_snap, double m, float* rho_out, DevCounters* ctr,
-                              cudaStream_t s);
+cudaError_t launch_build_tets(const Lattice& L, int n_snap, double m, float* rho_out, unsigned char* degen,
+                              DevCounters* ctr, cudaStream_t s);
 
 // ---- lt_bin.cu
 cudaError_t launch_bin_count(const Lattice& L, const FrameDev* d_frames, int n_frames, unsigned* d_count,

@@ -27,6 +27,7 @@ __device__ __forceinline__ void cube_fragments(const CubeProj& P, const FrameDev
       const float ax = axa + (float)shx, ay = aya + (float)shy;
 #pragma unroll
       for (int s = 0; s < 6; ++s) {
+        if (tet_degenerate(Lat, F.snapshot, cube, s)) continue;  // zero volume: contributes nothing
         const int c0 = tet_corner(s, 0), c1 = tet_corner(s, 1), c2 = tet_corner(s, 2), c3 = tet_corner(s, 3);
         const float txmin = fminf(fminf(P.x[c0], P.x[c1]), fminf(P.x[c2], P.x[c3]));
         const float txmax = fmaxf(fmaxf(P.x[c0], P.x[c1]), fmaxf(P.x[c2], P.x[c3]));

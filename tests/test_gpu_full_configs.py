@@ -1,0 +1,148 @@
+"""GPU parity at the full workload sizes, on outputs the oracle can compute
+one by one: crops of full frames, and gradient components of sampled
+particles.
+
+* 256^3 lattice, 8 snapshots x 16 perspective cameras at 2048^2, rendered
+  the way the benchmark times it (autotuned tile shape, one CUDA graph
+  replay of all 128 frames): crops of three frames against the oracle.
+* 512^3 lattice stored as float16 offsets, orthographic at 4096^2: 64
+  random 256^2 crops against the oracle on the decoded positions, and the
+  frame mass of the periodic box window against the total mass (1) to the
+  accuracy of pixel-centre sampling.
+* 64^3 lattice, 512^2, L2 loss against the render of a differently seeded
+  field: the adjoint on 256 random particles against the oracle's FP64
+  gradient and against central differences of the oracle's FP64 loss. The
+  step is h = 1e-6 box units: at 1e-4 the differences straddle the kinks of
+  the piecewise-linear chords (pixel centres crossing projected edges) and
+  are off by up to a few percent on some components, while the analytic
+  gradient and differences at 1e-5 .. 1e-7 agree to 1e-7.
+
+Tolerances are those of the other parity tests: 1e-4 of max(pixel, mean
+column density) per pixel, 1e-3 relative l2 for gradients.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from fd_local import incident_tets, local_image
+from lt_inputs import (ZeldovichField, config, decode_fp16_offsets, fp16_offsets, ortho_z,
+                       sphere_cameras)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PIX_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1208_3206_gb300.render import Renderer
+    return Renderer()
+
+
+def crop_error(img, refs, crops, mean_cd):
+    worst = 0.0
+    for (x, y, w, h), ref in zip(crops, refs):
+        got = img[y:y + h, x:x + w].astype(np.float64)
+        worst = max(worst, float((np.abs(got - ref) / np.maximum(np.abs(ref), mean_cd)).max()))
+    return worst
+
+
+def test_headline_workload_crops_of_graph_replay(R):
+    c = config("zel256_persp2048x128")
+    N, W, H = c["N"], c["W"], c["H"]
+    f = ZeldovichField.generate(N, c["n_index"], c["k_cut"], c["seed"])
+    pos = np.empty((len(c["lams"]), N ** 3, 4), dtype=np.float32)
+    for s, lam in enumerate(c["lams"]):
+        pos[s] = f.positions(lam)
+    del f
+    cams0 = sphere_cameras(16, W, H, radius=c["radius"], fov_y_deg=c["fov_y_deg"])
+    cams = [cam for _ in c["lams"] for cam in cams0]
+    snaps = [s for s in range(len(c["lams"])) for _ in cams0]
+    R.build_tets(torch.from_numpy(pos).cuda(), N)
+    tune = list(range(0, len(cams), 16))
+    R.autotune([cams[q] for q in tune], [snaps[q] for q in tune], reps=1)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        img = R.graph_build(cams, snaps, stream=stream)
+        R.graph_launch(stream)
+        R.sync()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3003)
+    size = 160
+    for fr in (0, 7 * 16 + 5, 4 * 16 + 11):
+        lo, hi = W // 2 - 420, W // 2 + 420 - size
+        crops = [(int(x), int(y), size, size) for x, y in rng.integers(lo, hi + 1, size=(2, 2))]
+        refs, nf, _ = oracle.render_crops(pos[snaps[fr]], N, cams[fr], crops)
+        assert nf > 0
+        nz = np.concatenate([r[r > 0] for r in refs])
+        got = img[fr].cpu().numpy()
+        assert crop_error(got, refs, crops, float(nz.mean())) <= PIX_TOL, fr
+    st = R.get_stats()
+    assert st["queue_overflow"] == 0
+
+
+def test_fp16_512_workload_random_crops(R):
+    c = config("zel512_fp16_ortho4096")
+    N, W, H = c["N"], c["W"], c["H"]
+    f = ZeldovichField.generate(N, c["n_index"], c["k_cut"], c["seed"])
+    off = fp16_offsets(f.displacement(c["lams"][0]), N)
+    del f
+    cam = ortho_z(W, H)
+    R.build_tets(torch.from_numpy(off).cuda(), N)
+    R.project_bin([cam])
+    img_t, m = R.render_tiles(with_mass=True)
+    img = img_t[0].cpu().numpy()
+    mass = float(m.cpu().numpy()[0])
+    del img_t
+    # the periodic box window holds the whole mass; pixel-centre samples
+    # integrate it to O((pixel / cell)^2), about 5e-5 at 8 pixels per cell
+    assert abs(mass - 1.0) <= 1e-3
+    dec = decode_fp16_offsets(off, N)
+    rng = np.random.default_rng(c["crop_seed"])
+    s = c["crop_size"]
+    crops = [(int(x), int(y), s, s) for x, y in rng.integers(0, W - s + 1, size=(c["crops"], 2))]
+    refs, nf, _ = oracle.render_crops(dec, N, cam, crops)
+    assert nf > 0
+    assert crop_error(img, refs, crops, 1.0) <= PIX_TOL
+
+
+def test_gradient_workload_against_oracle_and_central_differences(R):
+    c = config("zel64_grad512")
+    N, W, H = c["N"], c["W"], c["H"]
+    pos = ZeldovichField.generate(N, c["n_index"], c["k_cut"], c["seed"]).positions(c["lams"][0])
+    tpos = ZeldovichField.generate(N, c["n_index"], c["k_cut"], c["target_seed"]).positions(c["lams"][0])
+    cam = ortho_z(W, H)
+    target = oracle.render(tpos, N, cam)
+    base = oracle.render(pos, N, cam)
+    dLdI = 2.0 * (base - target)
+    R.build_tets(torch.from_numpy(pos).cuda(), N)
+    R.project_bin([cam])
+    R.render_tiles()
+    g_gpu = R.render_backward(torch.from_numpy(dLdI.astype(np.float32))[None].cuda())
+    g_gpu = g_gpu.cpu().numpy().reshape(N ** 3, 3).astype(np.float64)
+    g_ref = oracle.gradient(pos, N, cam, dLdI)
+    rng = np.random.default_rng(c["grad_seed"])
+    parts = rng.choice(N ** 3, size=c["grad_particles"], replace=False)
+    a, b = g_gpu[parts].ravel(), g_ref[parts].ravel()
+    assert np.linalg.norm(a - b) <= GRAD_TOL * np.linalg.norm(b)
+    # central differences of the oracle's loss L = sum (I - T)^2; moving one
+    # particle changes only its 48 incident tetrahedra
+    h = 1e-6
+    pos64 = pos[:, :3].astype(np.float64)
+    fd = []
+    for p in parts:
+        tets = incident_tets(int(p), N)
+        rest = base - local_image(pos64, N, tets, cam) - target
+        for ax in range(3):
+            pp = pos64.copy()
+            pp[p, ax] += h
+            up = local_image(pp, N, tets, cam)
+            pp[p, ax] -= 2 * h
+            dn = local_image(pp, N, tets, cam)
+            fd.append(float(np.sum((up - dn) * (up + dn + 2.0 * rest))) / (2 * h))
+    fd = np.array(fd)
+    assert np.linalg.norm(a - fd) <= GRAD_TOL * np.linalg.norm(fd)
