@@ -779,10 +779,14 @@ __device__ __forceinline__ float max_edge_slope(const TetRaster& t) {
                fmaxf(fabsf(t.a[2]) + fabsf(t.b[2]), fabsf(t.a[3]) + fabsf(t.b[3])));
 }
 
-// True when some fragment of a set-up tetrahedron may need the exact path.
+// True when some fragment of a set-up tetrahedron may need the exact path:
+// with A the largest position term and B v the round-off term over values
+// v <= hmax, some v has A + B v > kFragTol max(v, sigma). Below sigma that
+// needs A + B min(hmax, sigma) > kFragTol sigma; above it, B >= kFragTol.
 __device__ __forceinline__ bool may_need_exact(const TetRaster& t, float sigma_units, float delta) {
   const float stmax = fmaxf(fmaxf(t.st[0], t.st[1]), fmaxf(t.st[2], t.st[3]));
-  return max_edge_slope(t) * delta * t.vscale + stmax * kFragErr * t.hmax > kFragTol * fminf(t.hmax, sigma_units);
+  const float A = max_edge_slope(t) * delta * t.vscale, B = stmax * kFragErr;
+  return A + B * fminf(t.hmax, sigma_units) > kFragTol * sigma_units || (t.hmax > sigma_units && B >= kFragTol);
 }
 
 // True when the vertex uncertainty could move a pixel whose value matters

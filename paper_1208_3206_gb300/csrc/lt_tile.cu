@@ -125,8 +125,9 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
         const unsigned rel = cr + (unsigned)lane;  // < 38
         const long long cube = (long long)a.list[e0 + cq + rel / 6u];
         const int s = (int)(rel % 6u);
-        ok = !tet_degenerate(a.L, F.snapshot, cube, s) &&
-             (persp ? project_tet<true>(a.L, F, cube, s, P) : project_tet<false>(a.L, F, cube, s, P));
+        const bool zero_volume = tet_degenerate(a.L, F.snapshot, cube, s);  // load issued alongside the vertices
+        ok = persp ? project_tet<true>(a.L, F, cube, s, P) : project_tet<false>(a.L, F, cube, s, P);
+        ok = ok && !zero_volume;
       }
       float bx0 = 0.f, bx1 = -1.f, by0 = 0.f, by1 = -1.f;
       int sx0 = 0, sx1 = -1, sy0 = 0, sy1 = -1;
