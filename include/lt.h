@@ -109,7 +109,7 @@ typedef struct {
   long long behind_eye;      /* cubes skipped because a vertex is behind the eye */
   long long range_overflow;  /* pixels that left the accumulator range */
   long long exact_fragments; /* ill-conditioned fragments re-evaluated in FP64 (cumulative) */
-  long long queue_overflow;  /* such fragments left in FP32 because a tile's queue was full */
+  long long queue_overflow;  /* such fragments left in FP32 because a CTA's queue (32768 per tile) was full */
   int n_frames;              /* frames of the last lt_project_bin */
   int tile;                  /* tile edge in use */
   int graph_kernels;         /* kernel nodes in the graph of the last lt_graph_build */
@@ -138,8 +138,10 @@ lt_status lt_get_config(const lt_ctx* ctx, lt_config* out);
  * signed volume V (FP32 from displacement differences, recomputed in FP64
  * when |V| < 0.1 of a lattice cell, where the FP32 error bound would pass
  * 1e-5; this covers every near-degenerate sheet tetrahedron at caustics) and
- * rho = m / |V| (0 when V == 0). If d_rho is not NULL it
- * receives rho as float [n_snapshots][6 N^3] (tetrahedron id order).
+ * rho = m / |V| (0 when V == 0). Tetrahedra with V == 0 are marked in a
+ * context-owned mask (one byte per cube and snapshot) and contribute nothing
+ * to any later render. If d_rho is not NULL it receives rho as float
+ * [n_snapshots][6 N^3] (tetrahedron id order).
  * Errors: LT_ERR_ARG (N < 1, N^3 > 2^31, box <= 0, total_mass <= 0,
  * n_snapshots < 1, unknown pos_fmt, misaligned d_pos); non-finite positions
  * latch LT_ERR_NONFINITE.
