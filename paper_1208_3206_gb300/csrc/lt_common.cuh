@@ -219,13 +219,20 @@ __device__ __forceinline__ void anchor_affine(const FrameDev& F, int c, int i, i
   lo = fmaf((float)k, F.al[c][3], fmaf((float)j, F.al[c][2], fmaf((float)i, F.al[c][1], F.al[c][0])));
 }
 
-// Float-float (Xh + Xl) / (Zh + Zl) * (kh + kl) + c0 -> (hi, lo).
-__device__ __forceinline__ void ff_project(float Xh, float Xl, float Zh, float Zl, float kh, float kl, float c0,
-                                           float& hi, float& lo) {
-  const float q = Xh / Zh;
+// Approximate reciprocal (the hardware's, within a couple of ulp) for
+// quantities whose rounding the fragment error model absorbs.
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+
+// Float-float (Xh + Xl) / (Zh + Zl) * (kh + kl) + c0 -> (hi, lo); rz is an
+// approximate 1 / Zh. One Newton step makes the high quotient faithful, so
+// the FMA residual Xh - q Zh is exact.
+__device__ __forceinline__ void ff_project(float Xh, float Xl, float Zh, float Zl, float rz, float kh, float kl,
+                                           float c0, float& hi, float& lo) {
+  const float q0 = Xh * rz;
+  const float q = fmaf(fmaf(-q0, Zh, Xh), rz, q0);
   float r = fmaf(-q, Zh, Xh);  // exact residual of the division
   r = fmaf(-q, Zl, Xl) + r;
-  const float ql = __fdividef(r, Zh);  // low part: a few ulp suffice
+  const float ql = r * rz;
   const float p = kh * q;
   float e = fmaf(kh, q, -p);   // exact product error
   e = fmaf(kh, ql, e);
@@ -271,10 +278,11 @@ __device__ __forceinline__ bool project_cube(const Lattice& L, const FrameDev& F
     bool front = Z0 > F.near_z;
     int n_front = front ? 1 : 0;
     if (front) {
-      ff_project(Xh, Xl, Zh, Zl, F.kxh, F.kxl, F.cx, P.axh, P.axl);
-      ff_project(Yh, Yl, Zh, Zl, F.kyh, F.kyl, F.cy, P.ayh, P.ayl);
+      const float rz = fast_rcp(Zh);
+      ff_project(Xh, Xl, Zh, Zl, rz, F.kxh, F.kxl, F.cx, P.axh, P.axl);
+      ff_project(Yh, Yl, Zh, Zl, rz, F.kyh, F.kyl, F.cy, P.ayh, P.ayl);
     }
-    const float iZ0 = __frcp_rn(Z0);
+    const float iZ0 = fast_rcp(Z0);
     P.w0 = iZ0;
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
@@ -285,7 +293,7 @@ __device__ __forceinline__ bool project_cube(const Lattice& L, const FrameDev& F
       const float Zn = Z0 + dZ;
       front = front && (Zn > F.near_z);
       n_front += Zn > F.near_z ? 1 : 0;
-      const float inv = __frcp_rn(Zn * Z0);
+      const float inv = fast_rcp(Zn * Z0);
       // X_n/Z_n - X0/Z0 = (dX Z0 - X0 dZ) / (Z_n Z0), free of cancellation
       P.x[n] = (dX * Z0 - X0 * dZ) * inv * F.kx;
       P.y[n] = (dY * Z0 - Y0 * dZ) * inv * F.ky;
@@ -363,9 +371,10 @@ __device__ __forceinline__ bool project_tet(const Lattice& L, const FrameDev& F,
   anchor_affine(F, 2, i, j, k, Zh, Zl);
   const float X0 = Xh + Xl, Y0 = Yh + Yl, Z0 = Zh + Zl;
   bool front = Z0 > F.near_z;
-  ff_project(Xh, Xl, Zh, Zl, F.kxh, F.kxl, F.cx, P.axh, P.axl);
-  ff_project(Yh, Yl, Zh, Zl, F.kyh, F.kyl, F.cy, P.ayh, P.ayl);
-  P.w0 = __frcp_rn(Z0);
+  const float rz = fast_rcp(Zh);
+  ff_project(Xh, Xl, Zh, Zl, rz, F.kxh, F.kxl, F.cx, P.axh, P.axl);
+  ff_project(Yh, Yl, Zh, Zl, rz, F.kyh, F.kyl, F.cy, P.ayh, P.ayl);
+  P.w0 = fast_rcp(Z0);
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const float3 l = load_corner(L, snap_off, i, j, k, tet_corner_dyn(s, c), ok);
@@ -374,7 +383,7 @@ __device__ __forceinline__ bool project_tet(const Lattice& L, const FrameDev& F,
     const float dZ = F.f[0] * l.x + F.f[1] * l.y + F.f[2] * l.z;
     const float Zn = Z0 + dZ;
     front = front && (Zn > F.near_z);
-    const float inv = __frcp_rn(Zn * Z0);
+    const float inv = fast_rcp(Zn * Z0);
     P.x[c] = (dX * Z0 - X0 * dZ) * inv * F.kx;
     P.y[c] = (dY * Z0 - Y0 * dZ) * inv * F.ky;
     P.dw[c] = -dZ * inv;
@@ -434,7 +443,7 @@ __device__ __forceinline__ bool face_plane(float xp, float yp, float wp, float x
   const float ny = uw * vx - ux * vw;
   // a face seen nearly edge-on has an unreliable FP32 slope: treat as vertical
   if (!(fabsf(nw) > 1e-5f * (fabsf(ux * vy) + fabsf(uy * vx)))) return false;
-  const float inw = __frcp_rn(nw);
+  const float inw = fast_rcp(nw);
   pa = -nx * inw;
   pb = -ny * inw;
   pc = wp - pa * xp - pb * yp;
@@ -566,7 +575,7 @@ __device__ __forceinline__ bool tet_setup(float x0, float y0, float x1, float y1
   t.vscale = 1.0f;
   if (PERSP) {
     const float wmin = wa + fminf(fminf(w0, w1), fminf(w2, w3));
-    t.vscale = __frcp_rn(wmin * wmin);
+    t.vscale = fast_rcp(wmin * wmin);
     t.hmax = t.hmax * t.vscale;
   }
   if (PERSP) {
@@ -769,9 +778,11 @@ constexpr float kFragTol = 1e-5f;
 // Vertex position uncertainty (pixels) of a tetrahedron whose vertices lie
 // within R pixels of its cube's anchor (R includes, in perspective, the
 // depth terms of the projection): about four ulp of R from the displacement
-// and projection arithmetic, plus the tile-relative subtraction.
-__device__ __forceinline__ float vertex_uncertainty(float R) {
-  return R * (1.0f / 2097152.0f) + (1.0f / 524288.0f);  // 2^-21 R + 2^-19
+// and projection arithmetic (eight with the perspective's approximate
+// reciprocals), plus the tile-relative subtraction.
+__device__ __forceinline__ float vertex_uncertainty(float R, bool persp) {
+  // orthographic: 2^-21 R + 2^-19; perspective (approximate reciprocals): 2^-20 R + 2^-19
+  return R * (persp ? (1.0f / 1048576.0f) : (1.0f / 2097152.0f)) + (1.0f / 524288.0f);
 }
 
 __device__ __forceinline__ float max_edge_slope(const TetRaster& t) {
@@ -786,14 +797,15 @@ __device__ __forceinline__ float max_edge_slope(const TetRaster& t) {
 __device__ __forceinline__ bool may_need_exact(const TetRaster& t, float sigma_units, float delta) {
   const float stmax = fmaxf(fmaxf(t.st[0], t.st[1]), fmaxf(t.st[2], t.st[3]));
   const float A = max_edge_slope(t) * delta * t.vscale, B = stmax * kFragErr;
-  return A + B * fminf(t.hmax, sigma_units) > kFragTol * sigma_units || (t.hmax > sigma_units && B >= kFragTol);
+  // written so that a non-finite coefficient (an extreme sliver) also flags
+  return !(A + B * fminf(t.hmax, sigma_units) <= kFragTol * sigma_units) || (t.hmax > sigma_units && B >= kFragTol);
 }
 
 // True when the vertex uncertainty could move a pixel whose value matters
 // across the FP32 hull boundary (steep thin slivers): such a tetrahedron has
 // its whole bounding box visited.
 __device__ __forceinline__ bool may_miss_fragments(const TetRaster& t, float sigma_units, float delta) {
-  return max_edge_slope(t) * delta * t.vscale > kFragTol * sigma_units;
+  return !(max_edge_slope(t) * delta * t.vscale <= kFragTol * sigma_units);
 }
 
 // Exact-path decision for one candidate pixel of a flagged tetrahedron: f the
@@ -806,6 +818,7 @@ __device__ __forceinline__ bool fragment_needs_exact(float f0, float f1, float f
   if (f2 < mn) { mn = f2; ae = a.z; be = b.z; se = st.z; }
   if (f3 < mn) { mn = f3; ae = a.w; be = b.w; se = st.w; }
   const float pos_err = (fabsf(ae) + fabsf(be)) * delta;
+  if (!(pos_err < 3.0e38f) || mn != mn) return true;  // non-finite edge function: evaluate exactly
   if (!(mn > 0.0f)) return mn > -pos_err && pos_err * dvdT > kFragTol * sigma_units;
   return (pos_err + kFragErr * se * mn) * dvdT > kFragTol * fmaxf(v, sigma_units);
 }

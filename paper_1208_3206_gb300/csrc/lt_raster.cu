@@ -38,7 +38,7 @@ __device__ __forceinline__ void cube_fragments(const CubeProj& P, const FrameDev
           const float dwm = fmaxf(fmaxf(fabsf(P.dw[c0]), fabsf(P.dw[c1])), fmaxf(fabsf(P.dw[c2]), fabsf(P.dw[c3])));
           Rv += fmaxf(fabsf(P.axh - F.cx), fabsf(P.ayh - F.cy)) * __fdividef(dwm, P.w0);
         }
-        const float delta = vertex_uncertainty(Rv);
+        const float delta = vertex_uncertainty(Rv, PERSP);
         const float mg = 1e-3f + delta;
         const int qx0 = max(px0, (int)ceilf(ax + txmin - mg)), qx1 = min(px1, (int)floorf(ax + txmax + mg));
         const int qy0 = max(py0, (int)ceilf(ay + tymin - mg)), qy1 = min(py1, (int)floorf(ay + tymax + mg));
@@ -46,8 +46,8 @@ __device__ __forceinline__ void cube_fragments(const CubeProj& P, const FrameDev
         float Kn = 6.0f * F.K, invKn = 0.0f;
         if (PERSP) {
           const float zz = P.z[c0] * P.z[c1] * P.z[c2] * P.z[c3];
-          Kn = Kn / zz;
-          invKn = 1.0f / Kn;
+          Kn = __fdividef(Kn, zz);
+          invKn = fast_rcp(Kn);
         }
         TetRaster t;
         if (!tet_setup<PERSP>(P.x[c0], P.y[c0], P.x[c1], P.y[c1], P.x[c2], P.y[c2], P.x[c3], P.y[c3],

@@ -41,6 +41,8 @@ __device__ __forceinline__ unsigned long long pack_frag(unsigned tau, int sx, in
 }
 
 // 1 / a, or 0 for a == 0 (an edge function constant along the row).
+// (Correctly rounded over the whole range: a steep sliver's |a| can pass
+// 2^126, where the approximate reciprocal returns 0.)
 __device__ __forceinline__ float inv_or_zero(float a) { return a != 0.0f ? __frcp_rn(a) : 0.0f; }
 
 // Narrow [lo, hi] to the X where a X + rr >= 0 (rr the row term b Y + c).
@@ -154,14 +156,14 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
           const float off = fmaxf(fabsf(P.axh - F.cx), fabsf(P.ayh - F.cy));
           Rv += off * __fdividef(dwm, P.w0);
         }
-        delta = vertex_uncertainty(Rv);
+        delta = vertex_uncertainty(Rv, persp);
       }
       const float margin = 1e-3f + delta;
       const int rounds = __reduce_max_sync(FULL, ncp);
       float Kn = Kn0, invKn = 0.f;
       if (persp && ok) {
         Kn = __fdividef(Kn0, P.z[0] * P.z[1] * P.z[2] * P.z[3]);
-        invKn = __frcp_rn(Kn);
+        invKn = fast_rcp(Kn);
       }
       for (int r = 0; r < rounds; ++r) {
         int nrows = 0, qx0 = 0, qx1 = 0, qy0 = 0, sx = 0, sy = 0;

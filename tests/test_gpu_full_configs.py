@@ -107,7 +107,34 @@ def test_fp16_512_workload_random_crops(R):
     crops = [(int(x), int(y), s, s) for x, y in rng.integers(0, W - s + 1, size=(c["crops"], 2))]
     refs, nf, _ = oracle.render_crops(dec, N, cam, crops)
     assert nf > 0
-    assert crop_error(img, refs, crops, 1.0) <= PIX_TOL
+    # FP16 offsets put vertices on a 1/8-pixel grid, so some pixel centres lie
+    # exactly on the projection of a face parallel to the rays, where the
+    # column density jumps and the value at the centre is ambiguous. Pixels
+    # off by more than the tolerance must be such points: their value has to
+    # lie between the oracle's one-sided limits (rays moved by 1e-4 pixel in
+    # the eight axis and diagonal directions, which covers a centre on two
+    # such edges at once).
+    bad = []
+    for (x, y, w, h), ref in zip(crops, refs):
+        got = img[y:y + h, x:x + w].astype(np.float64)
+        e = np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)
+        for iy, ix in zip(*np.nonzero(e > PIX_TOL)):
+            bad.append((x + ix, y + iy, float(got[iy, ix]), float(ref[iy, ix])))
+    assert len(bad) <= 2e-3 * len(crops) * s * s
+    if bad:
+        one = [(bx, by, 1, 1) for bx, by, _, _ in bad]
+        eps = 1e-4 / W
+        limits = []
+        for dx, dy in ((eps, 0.0), (-eps, 0.0), (0.0, eps), (0.0, -eps), (eps, eps), (eps, -eps), (-eps, eps),
+                       (-eps, -eps)):
+            shifted = dict(cam, lo=(dx, dy), hi=(1.0 + dx, 1.0 + dy))
+            limits.append([r[0, 0] for r in oracle.render_crops(dec, N, shifted, one)[0]])
+        limits = np.array(limits)
+        for q, (bx, by, got, ref) in enumerate(bad):
+            lo_v, hi_v = min(limits[:, q].min(), ref), max(limits[:, q].max(), ref)
+            tol = PIX_TOL * max(abs(ref), 1.0)
+            assert hi_v - lo_v > tol, (bx, by, got, ref)  # a genuine jump, not an error
+            assert lo_v - tol <= got <= hi_v + tol, (bx, by, got, ref, lo_v, hi_v)
 
 
 def test_gradient_workload_against_oracle_and_central_differences(R):
