@@ -350,33 +350,63 @@ def run_lt(args, rank: int, world: int):
     }
     if atomic is not None:
         line["atomic"] = atomic
-    return line, (c, pos_np, cams, snaps)
+    # the GPU's pixels of frame 0's central crop (from the last end-to-end
+    # step's host copy), for the parity figure next to the CPU baseline
+    x0c, y0c, wc, hc = central_crop(cams[0], args.cpu_sample_crop)
+    gpu_crop = host_img[0, y0c:y0c + hc, x0c:x0c + wc].numpy().copy()
+    return line, (c, pos_np, cams, snaps, gpu_crop)
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle
 
 
+def central_crop(cam, crop: int):
+    """(x0, y0, w, h) of the central crop x crop window of a frame."""
+    W, H = cam["W"], cam["H"]
+    crop = min(crop, W, H)
+    return ((W - crop) // 2, (H - crop) // 2, crop, crop)
+
+
 def oracle_sample(c, pos_np, cams, snaps, crop: int, frame: int = 0):
-    """Time the FP64 oracle on one crop of one frame; returns (fragments, seconds)."""
+    """Time the FP64 oracle on the central crop of one frame; returns
+    (fragments, seconds, crop image)."""
     import oracle
 
     N = c["N"]
     cam = cams[frame]
     s = snaps[frame]
-    W, H = cam["W"], cam["H"]
-    x0, y0 = (W - crop) // 2, (H - crop) // 2
     t = time.perf_counter()
-    _, nf, _ = oracle.render_crops(pos_np[s], N, cam, [(x0, y0, crop, crop)])
-    return nf, time.perf_counter() - t
+    imgs, nf, _ = oracle.render_crops(pos_np[s], N, cam, [central_crop(cam, crop)])
+    return nf, time.perf_counter() - t, imgs[0]
 
 
-def cpu_baseline(c, pos_np, cams, snaps, crop: int):
-    nf, sec = oracle_sample(c, pos_np, cams, snaps, crop)
+def crop_parity(ref, got, tol: float = 1e-4) -> dict:
+    """Largest error of a GPU crop against the oracle's, relative to
+    max(pixel, mean column density of the crop's nonzero oracle pixels)."""
+    import numpy as np
+
+    ref = np.asarray(ref, dtype=np.float64)
+    got = np.asarray(got, dtype=np.float64)
+    nz = ref[ref > 0]
+    mean_cd = float(nz.mean()) if nz.size else 1.0
+    err = float((np.abs(got - ref) / np.maximum(np.abs(ref), mean_cd)).max()) if ref.size else 0.0
+    return {"max_rel_err": err, "tol": tol, "pass": err <= tol}
+
+
+def cpu_baseline(c, pos_np, cams, snaps, crop: int, gpu_crop=None):
+    """The oracle timed on the central crop of frame 0 (the CPU baseline);
+    with the GPU's pixels of the same crop, also their parity."""
+    nf, sec, ref = oracle_sample(c, pos_np, cams, snaps, crop)
     cores = os.cpu_count()
-    return {"value": nf / sec, "unit": "fragments/s", "cores": cores, "kind": "oracle",
-            "sample": f"frame 0, central {crop}x{crop} crop ({nf} fragments, {sec:.1f} s incl. the scan of all "
+    x0, y0, w, h = central_crop(cams[0], crop)
+    base = {"value": nf / sec, "unit": "fragments/s", "cores": cores, "kind": "oracle",
+            "sample": f"frame 0, central {w}x{h} crop ({nf} fragments, {sec:.1f} s incl. the scan of all "
                       f"{6 * c['N'] ** 3} tetrahedra)"}
+    parity = None
+    if gpu_crop is not None:
+        parity = dict(crop_parity(ref, gpu_crop), frame=0, crop=[x0, y0, w, h])
+    return base, parity
 
 
 def max_over_ranks(values, device):
@@ -400,7 +430,7 @@ def run_reference(args, rank: int, world: int):
         oracle_sample(c, pos_np, cams, snaps, min(64, args.cpu_sample_crop), w % len(cams))
     tot_f, tot_s = 0, 0.0
     for st in range(args.steps):
-        nf, sec = oracle_sample(c, pos_np, cams, snaps, args.cpu_sample_crop, st % len(cams))
+        nf, sec, _ = oracle_sample(c, pos_np, cams, snaps, args.cpu_sample_crop, st % len(cams))
         tot_f += nf
         tot_s += sec
     value = tot_f / tot_s
@@ -436,7 +466,8 @@ def main():
     line, wl = run_lt(args, rank, world)
     if rank == 0 and not args.no_cpu_baseline:
         log("CPU oracle sample")
-        line["cpu_baseline"] = cpu_baseline(*wl, crop=args.cpu_sample_crop)
+        c, pos_np, cams, snaps, gpu_crop = wl
+        line["cpu_baseline"], line["parity"] = cpu_baseline(c, pos_np, cams, snaps, args.cpu_sample_crop, gpu_crop)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:
