@@ -20,7 +20,7 @@
  *     by differentiating rho_i * dl_i directly (density through the volume,
  *     chord through the entry and exit face planes).
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *   - corner n of a cube is lattice point (i+(n&1), j+((n>>1)&1), k+((n>>2)&1));
  *   - the lattice is periodic: N^3 cubes, corner indices taken mod N, each
  *     vertex unwrapped to the minimum image of its Lagrangian position;
@@ -29,7 +29,10 @@
  *   - a tetrahedron with V == 0 exactly contributes nothing;
  *   - orthographic windows may be periodic in both image axes (wrap), in
  *     which case every periodic copy of a tetrahedron is drawn; perspective
- *     views draw the single unwrapped copy of the lattice.
+ *     views draw the single unwrapped copy of the lattice;
+ *   - the tetrahedron is closed: a ray lying exactly in the plane of a face
+ *     parallel to it counts the segment it shares with the face (the value
+ *     there is the upper one-sided limit of a jump).
  */
 #include <math.h>
 #include <stdlib.h>

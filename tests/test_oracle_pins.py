@@ -347,3 +347,20 @@ def test_local_difference_equals_full_render_difference():
             dn, Lm = local_image(pp, N, tets, cam), np.sum((oracle.render(pp, N, cam) - T) ** 2)
             local = np.sum((up - dn) * (up + dn + 2.0 * rest))
             assert local == pytest.approx(Lp - Lm, rel=1e-8, abs=1e-12 * max(1.0, abs(Lp)))
+
+
+def test_chord_jumps_across_a_face_parallel_to_the_ray():
+    """A face parallel to the view direction projects to a hull edge where the
+    chord jumps; on the face itself the closed tetrahedron gives the upper
+    one-sided limit. Corner tetrahedron (0,0,0), (a,0,0), (0,a,0), (0,0,a)
+    seen along z: its face x = 0 contains the z axis, and for a ray at
+    (x, y) with x, y >= 0 the chord is a - x - y."""
+    a, y = 1.0, 0.25
+    v = np.array([[0, 0, 0], [a, 0, 0], [0, a, 0], [0, 0, a]], dtype=np.float64)
+    eps = 1e-9
+    inside = oracle.chord(v, [eps, y, -3.0], [0, 0, 1])
+    outside = oracle.chord(v, [-eps, y, -3.0], [0, 0, 1])
+    on_face = oracle.chord(v, [0.0, y, -3.0], [0, 0, 1])
+    assert inside == pytest.approx(a - y - eps, abs=1e-12)
+    assert outside == 0.0
+    assert on_face == pytest.approx(a - y, abs=1e-12)
