@@ -400,6 +400,7 @@ lt_status render_impl(lt_ctx* ctx, float* d_image, double* d_mass, cudaStream_t 
   a.tile = ctx->tile;
   a.xq = ctx->d_xq;
   a.xq_cap = lt::kExactQueueCap;
+  a.list_cap = ctx->list_cap;
   const int threads = ctx->cfg.raster_threads;
   int cps = ctx->cfg.ctas_per_sm;
   const int fit = lt::raster_max_ctas_per_sm(threads, ctx->tile, ctx->any_persp);
@@ -585,6 +586,7 @@ lt_status lt_count_fragments(lt_ctx* ctx, long long* h_counts, lt_stream stream)
   a.tile = ctx->tile;
   a.xq = nullptr;  // counting queues nothing
   a.xq_cap = 0;
+  a.list_cap = ctx->list_cap;
   long long ctas = (long long)ctx->num_sms * 4;
   if (ctas > ctx->n_tiles) ctas = ctx->n_tiles;
   LT_CUDA(lt::launch_count_fragments(a, ctx->d_frag, ctx->n_frames, (int)ctas, 256, s));

@@ -39,6 +39,7 @@ struct RasterArgs {
   int tile;
   unsigned long long* xq;  // exact-evaluation queue, xq_cap entries per CTA
   unsigned xq_cap;
+  unsigned long long list_cap;  // entries the cube lists hold (reads are clamped to it)
 };
 cudaError_t launch_raster(const RasterArgs& a, int ctas, int threads, int any_persp, cudaStream_t s);
 int raster_max_ctas_per_sm(int threads, int tile, int any_persp);

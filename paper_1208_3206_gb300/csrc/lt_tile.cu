@@ -108,8 +108,16 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
     const int tyi = (int)(tl / F.tiles_x), txi = (int)(tl - (long long)tyi * F.tiles_x);
     const int tx0 = txi * T, ty0 = tyi * T;
     const int tw = min(T, F.W - tx0), th = min(T, F.H - ty0);
-    const unsigned long long e0 = a.off[tg];
-    const long long ntet = 6LL * (long long)(a.off[tg + 1] - e0);
+    // a graph replayed after the positions changed can need more list entries
+    // than it was sized for: the scatter dropped the excess (and latched the
+    // error), and the walk reads only what the lists hold
+    unsigned long long e0 = a.off[tg], e1 = a.off[tg + 1];
+    if (e1 > a.list_cap) {
+      if (threadIdx.x == 0) atomicOr(&a.ctr->errors, kErrCapacity);
+      e0 = min(e0, a.list_cap);
+      e1 = a.list_cap;
+    }
+    const long long ntet = 6LL * (long long)(e1 - e0);
     const bool wrap = (!persp) && F.wrap;
     const float Kn0 = 6.0f * F.K;
     const float sig = F.sigma_units;

@@ -148,7 +148,12 @@ def test_gradient_workload_against_oracle_and_central_differences(R):
     dLdI = 2.0 * (base - target)
     R.build_tets(torch.from_numpy(pos).cuda(), N)
     R.project_bin([cam])
-    R.render_tiles()
+    img, m = R.render_tiles(with_mass=True)
+    # the forward image of this workload in full, and its mass
+    got = img[0].cpu().numpy().astype(np.float64)
+    assert float((np.abs(got - base) / np.maximum(np.abs(base), 1.0)).max()) <= PIX_TOL
+    mass_ref = oracle.frame_mass(base, cam)
+    assert abs(float(m.cpu().numpy()[0]) - mass_ref) <= 1e-6 * mass_ref
     g_gpu = R.render_backward(torch.from_numpy(dLdI.astype(np.float32))[None].cuda())
     g_gpu = g_gpu.cpu().numpy().reshape(N ** 3, 3).astype(np.float64)
     g_ref = oracle.gradient(pos, N, cam, dLdI)

@@ -276,3 +276,40 @@ def test_mid_config_full_frame(R, name):
     assert abs(nf - nf_ref) <= 1e-4 * nf_ref
     img_a, _ = gpu_render(R, pos, c["N"], [cam], atomic=True)
     assert pixel_error(img_a[0], ref, 1.0) <= PIX_TOL
+
+
+def test_graph_replay_reports_bin_capacity_overflow():
+    """A graph's bin lists are sized when it is built. Replaying it after the
+    positions changed to a lattice that needs more list entries latches
+    LT_ERR_CAPACITY: the scatter checks every write against the capacity and
+    the raster reads only what the lists hold. (A fresh context, so that the
+    lists are sized by this graph alone.)"""
+    from paper_1208_3206_gb300._lib import LtError
+    from paper_1208_3206_gb300.render import Renderer
+    R = Renderer()
+    N = 16
+    f = field(N, -2.0, 6.0, 31)
+    calm = torch.from_numpy(f.positions(0.05)).cuda()
+    wild = torch.from_numpy(f.positions(4.0)).cuda()
+    cams = [ortho_z(256, 256)]
+    R.set_config(tile=8)
+    pos = calm.clone()
+    R.build_tets(pos, N)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        R.graph_build(cams)
+        R.graph_launch()
+        R.sync()
+        need_calm = R.get_stats()["entries"]
+        pos.copy_(wild)
+        R.graph_launch()
+        with pytest.raises(LtError) as e:
+            R.sync()
+    torch.cuda.synchronize()
+    assert e.value.name == "LT_ERR_CAPACITY"
+    # the same lattice binned directly fits (the pass sizes its lists)
+    R.build_tets(wild, N)
+    R.project_bin(cams)
+    R.render_tiles()
+    R.sync()
+    assert R.get_stats()["entries"] > need_calm
