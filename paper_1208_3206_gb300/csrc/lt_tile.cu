@@ -5,19 +5,22 @@
 // tile, each warp repeatedly takes 32 tetrahedra (one per lane) of the tile's
 // cube list:
 //   1. every lane projects its tetrahedron and builds its raster form (the
-//      per-tetrahedron setup of lt_common.cuh) in tile pixel coordinates,
-//      keeps it in a per-warp shared-memory record, and counts the pixel
-//      centres of its bounding box inside the tile;
-//   2. a warp scan turns the counts into one flat list of (tetrahedron,
-//      pixel) candidates;
-//   3. all 32 lanes walk that list together, 32 candidates per step (the
-//      owning tetrahedron of a candidate is found from a bit mask of the
-//      tetrahedra starting in the step), evaluate rho * dl at the pixel and
-//      add it to the tile's fixed-point accumulators in shared memory.
+//      per-tetrahedron setup of lt_common.cuh) in tile pixel coordinates;
+//      the records of the drawable ones are compacted into a per-warp table
+//      in shared memory;
+//   2. a warp scan flattens the (tetrahedron, row) jobs of their bounding
+//      boxes; 32 jobs at a time, each lane finds the pixel span of its row
+//      where every edge function is >= 0;
+//   3. a second scan flattens the spans' pixels; 32 pixels at a time, each
+//      lane evaluates rho * dl and adds it to the tile's fixed-point
+//      accumulators in shared memory (the owner of a job or pixel is found
+//      from the popcount of the step's start mask, without shared memory);
+//   4. fragments whose FP32 value may be off by more than the tolerance are
+//      queued and evaluated exactly in FP64 after the walk.
 // Control flow stays uniform across the warp, so lanes are busy in every
 // phase whatever the sizes of the tetrahedra. Integer accumulation makes
-// the result independent of the order of the adds. After the list is done
-// every pixel of the tile is converted and stored once.
+// the result independent of the order of the adds. After the walk every
+// pixel of the tile is converted and stored once.
 #include "lt_internal.h"
 
 namespace lt {
@@ -32,7 +35,6 @@ constexpr int kRec = 36;  // words per tetrahedron record (stride 4 mod 32: floa
 // (row spans); [5] pa0, pb0, pc0, pa1; [6] pb1, pc1, g (perspective depth
 // planes), exact-check flag; [7] edge steepness st[4]; [8] periodic copy
 // (sx, sy), lane, vertex uncertainty.
-
 
 __device__ __forceinline__ unsigned long long pack_frag(unsigned tau, int sx, int sy, int X, int Y) {
   return (unsigned long long)tau | ((unsigned long long)(unsigned)(sx + 64) << 32) |
