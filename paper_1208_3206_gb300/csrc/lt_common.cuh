@@ -613,19 +613,6 @@ __device__ __forceinline__ bool tet_setup(float x0, float y0, float x1, float y1
   return true;
 }
 
-// Value of a set-up tetrahedron at relative pixel (X, Y) with row terms
-// e_row[e] = b[e] Y + c[e] (and p_row for perspective).
-template <bool PERSP>
-__device__ __forceinline__ float tet_value(const TetRaster& t, float X, const float* erow, const float* prow) {
-  float T = fminf(fminf(fmaf(t.a[0], X, erow[0]), fmaf(t.a[1], X, erow[1])),
-                  fminf(fmaf(t.a[2], X, erow[2]), fmaf(t.a[3], X, erow[3])));
-  T = fmaxf(T, 0.0f);
-  if (!PERSP) return T;
-  const float M = fmaxf(fmaf(t.pa[0], X, prow[0]), fmaf(t.pa[1], X, prow[1]));
-  const float den = M * fmaf(t.g, T, M);
-  return __fdividef(T, den);
-}
-
 // Pixel span [lo, hi] (relative X) of row terms where every edge function is
 // >= 0, widened by a small margin so that rounding never drops a pixel.
 __device__ __forceinline__ void row_span(const TetRaster& t, const float* erow, float& lo, float& hi) {
