@@ -54,3 +54,12 @@ def test_status_strings_and_null_arguments(lib):
 def test_library_is_sm103a_only():
     from paper_1208_3206_gb300 import _build
     assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the compiled library the binding raises."""
+    from paper_1208_3206_gb300 import _build, _lib
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "missing" / "liblt.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="liblt.so not found"):
+        _lib.load()
