@@ -63,3 +63,14 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="liblt.so not found"):
         _lib.load()
+
+
+def test_frame_mass_static_argument_checks(lib):
+    """Argument and capacity errors come back before any CUDA call."""
+    import ctypes as C
+    fake = C.c_void_p(0x1000)  # never dereferenced: the checks return first
+    assert lib.lt_frame_mass_static(None, 1, 4, 4, 1.0, fake, None) == 1
+    assert lib.lt_frame_mass_static(fake, 0, 4, 4, 1.0, fake, None) == 1
+    assert lib.lt_frame_mass_static(fake, 1, 4, 4, 0.0, fake, None) == 1
+    assert lib.lt_frame_mass_static(fake, 1, 4, 4, float("nan"), fake, None) == 1
+    assert lib.lt_frame_mass_static(fake, 129, 4, 4, 1.0, fake, None) == 3
