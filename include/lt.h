@@ -60,7 +60,7 @@ typedef enum {
   LT_ERR_CUDA = 2,        /* a CUDA runtime call failed */
   LT_ERR_CAPACITY = 3,    /* a bin list outgrew its reserved capacity */
   LT_ERR_NONFINITE = 4,   /* a particle position is NaN or infinite */
-  LT_ERR_BEHIND_EYE = 5,  /* a perspective frame has a vertex at or behind the eye plane */
+  LT_ERR_BEHIND_EYE = 5,  /* a cube straddles the eye plane of a perspective frame */
   LT_ERR_RANGE = 6,       /* a pixel exceeded the fixed-point accumulator range */
   LT_ERR_STATE = 7,       /* calls made out of order (e.g. render before bin) */
   LT_ERR_NOMEM = 8        /* device allocation failed */
@@ -73,8 +73,10 @@ typedef enum { LT_ORTHO = 0, LT_PERSP = 1 } lt_camera_type;
  * LT_ORTHO: rays along fwd through the window [lo, hi] of the (right, up')
  *   coordinates of world points; wrap != 0 makes the window periodic (every
  *   periodic copy of a tetrahedron is drawn; use a window one box wide).
- * LT_PERSP: rays from eye; vertical field of view fov_y_deg, square pixels;
- *   every vertex must lie in front of the eye (LT_ERR_BEHIND_EYE).
+ * LT_PERSP: rays from eye (half-lines); vertical field of view fov_y_deg,
+ *   square pixels. A cube entirely behind the eye plane is not drawn (no ray
+ *   reaches it); a cube straddling the eye plane cannot be projected and
+ *   latches LT_ERR_BEHIND_EYE.
  * The view is set up in double precision on the host; each cube's projected
  * anchor point is carried to the kernels with about 2^-37 relative error, so
  * pixel positions are exact to well below a millionth of a pixel. */
@@ -106,7 +108,7 @@ typedef struct {
   long long fp64_fallbacks;  /* volumes recomputed in FP64 by lt_build_tets */
   long long inverted;        /* tetrahedra with V > 0 (orientation flipped vs t = 0) */
   long long nonfinite;       /* non-finite positions seen */
-  long long behind_eye;      /* cubes skipped because a vertex is behind the eye */
+  long long behind_eye;      /* cubes skipped because they straddle a perspective eye plane */
   long long range_overflow;  /* pixels that left the accumulator range */
   long long exact_fragments; /* ill-conditioned fragments re-evaluated in FP64 (cumulative) */
   long long queue_overflow;  /* such fragments left in FP32 because a CTA's queue (32768 per tile) was full */
@@ -172,7 +174,12 @@ lt_status lt_project_bin(lt_ctx* ctx, const lt_camera* cams, int n_frames, const
  * lt_project_bin. One persistent launch; each CTA takes (frame, tile) work
  * items, accumulates rho_t * dl_t of every tetrahedron of the tile's cubes
  * into on-chip fixed-point integer sums (so the image is bit-reproducible
- * whatever the order), and stores every pixel once.
+ * whatever the order), and stores every pixel once. Fragments whose FP32
+ * value may be off by more than 1e-5 of max(value, mean column density)
+ * (thin slivers, steep edges) are re-evaluated exactly in FP64 by clipping
+ * the pixel ray against the four faces; tetrahedra with V == 0 contribute
+ * nothing. A graph replay whose lists outgrew their capacity draws only the
+ * entries the lists hold and latches LT_ERR_CAPACITY.
  * d_image: float [n_frames][H][W] (caller owned). d_mass (may be NULL):
  * double [n_frames], per frame the sum of pixel values times the pixel area
  * (orthographic: window area / (W H); perspective: area on the image plane
