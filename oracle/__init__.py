@@ -14,4 +14,5 @@ from .oracle import (  # noqa: F401
     chord,
     tet_vertices,
     render_soup,
+    resample,
 )

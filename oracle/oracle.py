@@ -91,6 +91,8 @@ def _load():
         lib.orc_tet_vertices.restype = C.c_int
         lib.orc_render_soup.argtypes = [dp, dp, C.c_long, C.POINTER(_Cam), dp]
         lib.orc_render_soup.restype = C.c_int
+        lib.orc_resample.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, dp, C.c_int]
+        lib.orc_resample.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -211,4 +213,20 @@ def render_soup(verts, dens, cam) -> np.ndarray:
                              _ptr(out, C.c_double))
     if rc != 0:
         raise RuntimeError(f"oracle render_soup failed with code {rc}")
+    return out
+
+
+def resample(pos, N: int, n: int, weight: str = "density", box: float = 1.0, total_mass: float = 1.0,
+             nthreads: int = 0) -> np.ndarray:
+    """Resampling onto a periodic n^3 grid (Sec. 4.3, Eq. 10-12): cell
+    [c][b][a] holds the sum over tetrahedra of q dl, dl the length of the
+    cell's central line along z inside the tetrahedron and the cell's slab;
+    q = rho (weight "density") or 1 (weight "streams")."""
+    lib = _load()
+    p = _pos64(pos, N)
+    w = {"density": 0, "streams": 1}[weight]
+    out = np.zeros((n, n, n), dtype=np.float64)
+    rc = lib.orc_resample(_ptr(p, C.c_double), N, box, total_mass, n, w, _ptr(out, C.c_double), nthreads)
+    if rc != 0:
+        raise RuntimeError(f"oracle resample failed with code {rc}")
     return out

@@ -364,3 +364,56 @@ def test_chord_jumps_across_a_face_parallel_to_the_ray():
     assert inside == pytest.approx(a - y - eps, abs=1e-12)
     assert outside == 0.0
     assert on_face == pytest.approx(a - y, abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Resampling onto a grid (Sec. 4.3)
+
+
+def test_resample_unperturbed_lattice_is_uniform():
+    """One stream of density 1 everywhere: every cell holds rho g = g, in
+    both weights (grids chosen so no central line lies on a cube face)."""
+    N = 4
+    idx = np.arange(N ** 3)
+    pos = np.zeros((N ** 3, 4))
+    pos[:, 0], pos[:, 1], pos[:, 2] = idx % N / N, (idx // N) % N / N, idx // (N * N) / N
+    for n in (4, 8, 12):
+        np.testing.assert_allclose(oracle.resample(pos, N, n, "density"), 1.0 / n, atol=1e-15)
+        np.testing.assert_allclose(oracle.resample(pos, N, n, "streams"), 1.0 / n, atol=1e-15)
+
+
+def test_resample_pancake_along_z_closed_form():
+    """Displacement along z only, z = q_z - (A / 2 pi) sin(2 pi q_z) with
+    A > 1 (shell crossing, three streams). Cube k of every column maps onto
+    the box between z_k and z_{k+1}, with density h / |z_{k+1} - z_k|, so
+    each slab's value is a sum of interval overlaps."""
+    N, n, A = 8, 24, 1.6
+    h, g = 1.0 / N, 1.0 / n
+    idx = np.arange(N ** 3)
+    i, j, k = idx % N, (idx // N) % N, idx // (N * N)
+    pos = np.zeros((N ** 3, 4))
+    pos[:, 0], pos[:, 1] = i * h, j * h
+    pos[:, 2] = np.mod(k * h - A / (2 * np.pi) * np.sin(2 * np.pi * k * h), 1.0)
+    zk = np.arange(N + 1) * h - A / (2 * np.pi) * np.sin(2 * np.pi * np.arange(N + 1) * h)
+    dens, streams = np.zeros(n), np.zeros(n)
+    for q in range(N):
+        lo, hi = sorted((zk[q], zk[q + 1]))
+        for c in range(-n, 2 * n):
+            ov = max(0.0, min(hi, (c + 1) * g) - max(lo, c * g))
+            dens[c % n] += h / (hi - lo) * ov
+            streams[c % n] += ov
+    assert streams.max() > 2.5 * g  # three streams somewhere
+    np.testing.assert_allclose(oracle.resample(pos, N, n, "density"),
+                               np.broadcast_to(dens[:, None, None], (n, n, n)), atol=1e-12)
+    np.testing.assert_allclose(oracle.resample(pos, N, n, "streams"),
+                               np.broadcast_to(streams[:, None, None], (n, n, n)), atol=1e-13)
+
+
+def test_resample_columns_add_up_to_the_projection():
+    """Summing a column's slabs gives its whole chord sum: the orthographic
+    projection along z sampled at the same centres."""
+    N, n = 8, 16
+    pos = ZeldovichField.generate(N, -2.0, 3.0, 7).positions(1.8)
+    r = oracle.resample(pos, N, n, "density")
+    img = oracle.render(pos, N, ortho_z(n, n))
+    np.testing.assert_allclose(r.sum(axis=0), img, atol=1e-12 * img.max())
