@@ -631,17 +631,21 @@ __device__ __forceinline__ void row_span(const TetRaster& t, const float* erow, 
 }
 
 // Split a non-negative accumulator-unit value into the two 32-bit shared
-// counters of a pixel (low 16 bits and the rest). Integer sums are exact and
-// associative, so the image does not depend on the order of fragments.
+// counters of a pixel: the low kAccLoBits bits and the rest. Integer sums are
+// exact and associative, so the image does not depend on the order of
+// fragments. The pixel value is (hi << kAccLoBits) + lo; lo cannot wrap
+// before 2^(32 - kAccLoBits) = 262144 fragments land in one pixel.
+constexpr int kAccLoBits = 14;
+
 __device__ __forceinline__ void accum_fixed(unsigned* lo, unsigned* hi, float q, unsigned* err) {
   if (q < 4294967040.0f) {
     const unsigned u = __float2uint_rn(q);
     if (u) {
-      atomicAdd(lo, u & 0xFFFFu);
-      atomicAdd(hi, u >> 16);
+      atomicAdd(lo, u & ((1u << kAccLoBits) - 1u));
+      atomicAdd(hi, u >> kAccLoBits);
     }
   } else {
-    const float qh = q * (1.0f / 65536.0f);
+    const float qh = q * (1.0f / (float)(1u << kAccLoBits));
     if (qh < 4294967040.0f) {
       atomicAdd(hi, __float2uint_rn(qh));
     } else {

@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
     for (int li = threadIdx.x; li < tw * th; li += blockDim.x) {
       const int ly = li / tw, lx = li - ly * tw;
       const int si = ly * T + lx;
-      const unsigned long long q = ((unsigned long long)acc_hi[si] << 16) + (unsigned long long)acc_lo[si];
+      const unsigned long long q = ((unsigned long long)acc_hi[si] << kAccLoBits) + (unsigned long long)acc_lo[si];
       double v = (double)q * F.unit;
       if (persp) {
         const float xt = F.tan_x * (2.0f * ((float)(tx0 + lx) + 0.5f) / (float)F.W - 1.0f);
