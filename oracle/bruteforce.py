@@ -11,6 +11,8 @@ the oracle pins its arithmetic:
   * `render_cell_projection`: the front/back face form of Eq. 13 (Sec. 4.4):
     every face hit by the ray adds rho * |X - c| to a back-face sum or to a
     front-face sum, c the camera location; the pixel is back minus front.
+  * `resample_barycentric`: the grid resampling of Sec. 4.3 with the same
+    barycentric inside test along each cell column.
 
 Both draw every periodic copy of every tetrahedron for periodic orthographic
 windows by brute force over image-period shifts in [-2, 2].
@@ -183,3 +185,45 @@ def render_cell_projection(pos, N: int, cam: dict, box: float = 1.0, total_mass:
                 front += np.where(hit & (facing < 0), rho[t] * dist, 0.0)
                 back += np.where(hit & (facing > 0), rho[t] * dist, 0.0)
     return (back - front).reshape(cam["H"], cam["W"])
+
+
+def resample_barycentric(pos, N: int, n: int, weight: str = "density", box: float = 1.0,
+                         total_mass: float = 1.0) -> np.ndarray:
+    """Resampling onto the periodic n^3 grid (Sec. 4.3) by brute force: every
+    (cell column, tetrahedron, period shift) triple; the segment of the
+    column's central line inside the tetrahedron is the parameter interval on
+    which all four barycentric coordinates are >= 0, then clipped to each
+    slab. Cell [c][b][a] as in oracle.resample."""
+    verts, rho, _ = lattice_tets(pos, N, box, total_mass)
+    g = box / n
+    out = np.zeros((n, n, n))
+    cols = np.array([[(a + 0.5) * g, (b + 0.5) * g] for b in range(n) for a in range(n)])
+    d = np.tile(np.array([[0.0, 0.0, 1.0]]), (cols.shape[0], 1))
+    for t in range(verts.shape[0]):
+        if rho[t] == 0.0:
+            continue
+        q = rho[t] if weight == "density" else 1.0
+        v = verts[t]
+        M = np.vstack([v.T, np.ones(4)])
+        Minv = np.linalg.inv(M)
+        for sy in range(-2, 3):
+            for sx in range(-2, 3):
+                o = np.column_stack([cols[:, 0] + sx * box, cols[:, 1] + sy * box, np.zeros(cols.shape[0])])
+                lam0 = (Minv[:, :3] @ o.T) + Minv[:, 3:4]
+                mu = Minv[:, :3] @ d.T
+                lo = np.full(o.shape[0], -np.inf)
+                hi = np.full(o.shape[0], np.inf)
+                ok = np.ones(o.shape[0], dtype=bool)
+                for i in range(4):
+                    with np.errstate(divide="ignore", invalid="ignore"):
+                        s = -lam0[i] / mu[i]
+                    lo = np.where(mu[i] > 0, np.maximum(lo, s), lo)
+                    hi = np.where(mu[i] < 0, np.minimum(hi, s), hi)
+                    ok &= ~((mu[i] == 0) & (lam0[i] < 0))
+                for p in np.nonzero(ok & (hi > lo))[0]:
+                    a, b = p % n, p // n
+                    for c in range(int(math.floor(lo[p] / g)), int(math.floor(hi[p] / g)) + 1):
+                        seg = min(hi[p], (c + 1) * g) - max(lo[p], c * g)
+                        if seg > 0:
+                            out[c % n, b, a] += q * seg
+    return out

@@ -417,3 +417,14 @@ def test_resample_columns_add_up_to_the_projection():
     r = oracle.resample(pos, N, n, "density")
     img = oracle.render(pos, N, ortho_z(n, n))
     np.testing.assert_allclose(r.sum(axis=0), img, atol=1e-12 * img.max())
+
+
+def test_resample_matches_bruteforce_barycentric():
+    """orc_resample against the barycentric brute force on a small random
+    lattice (independent walk, unwrapping and inside test)."""
+    N, n = 3, 6
+    pos = ZeldovichField.generate(N, -2.0, 1.5, 11).positions(1.3).astype(np.float64)
+    for weight in ("density", "streams"):
+        a = oracle.resample(pos, N, n, weight)
+        b = bf.resample_barycentric(pos, N, n, weight)
+        np.testing.assert_allclose(a, b, atol=1e-12 * max(1.0, b.max()))
