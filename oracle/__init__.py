@@ -15,4 +15,5 @@ from .oracle import (  # noqa: F401
     tet_vertices,
     render_soup,
     resample,
+    point_density,
 )

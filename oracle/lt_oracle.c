@@ -588,3 +588,80 @@ int orc_resample(const double* pos, int N, double box, double total_mass, int n,
   free(bufs);
   return ORC_OK;
 }
+
+/*
+ * Point evaluation of the overlapping-streams density (Sec. 3.2, Eq. 4-5):
+ * for each point p (pts[3 P], in box coordinates, any period), the sum over
+ * the tetrahedra T_i containing p (any periodic copy) of q_i, with
+ * q_i = rho_i (weight 0: the total density rho_tot(p) of Eq. 4) or 1
+ * (weight 1: the number of streams at p). Every (point, tetrahedron) pair is
+ * tested, so it is meant for small point sets (slices, grid centres of small
+ * grids). Points exactly on a face count for both sides.
+ */
+int orc_point_density(const double* pos, int N, double box, double total_mass, const double* pts, long P,
+                      int weight, double* out, int nthreads) {
+  if (N <= 0 || box <= 0 || P < 0 || (weight != 0 && weight != 1)) return ORC_ERR_ARG;
+  const int T = num_threads(nthreads);
+  double* bufs = (double*)calloc((size_t)T * (P > 0 ? P : 1), sizeof(double));
+  const double m = total_mass / (6.0 * (double)N * N * N);
+  const long ncubes = (long)N * N * N;
+#pragma omp parallel num_threads(T)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double* acc = bufs + (size_t)tid * (P > 0 ? P : 1);
+#pragma omp for schedule(static)
+    for (long cube = 0; cube < ncubes; ++cube) {
+      long i = cube % N, j = (cube / N) % N, k = cube / ((long)N * N);
+      for (int s = 0; s < 6; ++s) {
+        double v[4][3];
+        tet_vertices(pos, N, box, i, j, k, s, v);
+        const double V = tet_volume(v);
+        if (V == 0.0) continue;
+        const double q = weight == 0 ? m / fabs(V) : 1.0;
+        /* outward face planes: inside means n_f . (p - a_f) <= 0 for all f */
+        double nrm[4][3], base[4][3];
+        for (int f = 0; f < 4; ++f) {
+          const double *a = v[(f + 1) & 3], *b = v[(f + 2) & 3], *c = v[(f + 3) & 3];
+          double e1[3], e2[3], t[3];
+          sub3(b, a, e1); sub3(c, a, e2);
+          cross3(e1, e2, nrm[f]);
+          sub3(v[f], a, t);
+          if (dot3(nrm[f], t) > 0.0) { nrm[f][0] = -nrm[f][0]; nrm[f][1] = -nrm[f][1]; nrm[f][2] = -nrm[f][2]; }
+          memcpy(base[f], a, sizeof base[f]);
+        }
+        double lo[3], hi[3];
+        for (int c = 0; c < 3; ++c) {
+          lo[c] = fmin(fmin(v[0][c], v[1][c]), fmin(v[2][c], v[3][c]));
+          hi[c] = fmax(fmax(v[0][c], v[1][c]), fmax(v[2][c], v[3][c]));
+        }
+        for (long p = 0; p < P; ++p) {
+          /* the periodic copy of the point nearest the tetrahedron's box */
+          double x[3];
+          int in_box = 1;
+          for (int c = 0; c < 3; ++c) {
+            double xc = pts[3 * p + c];
+            xc -= box * floor((xc - lo[c]) / box);  /* into [lo, lo + box) */
+            x[c] = xc;
+            if (xc > hi[c]) in_box = 0;
+          }
+          if (!in_box) continue;
+          int inside = 1;
+          for (int f = 0; f < 4 && inside; ++f) {
+            double t[3];
+            sub3(x, base[f], t);
+            if (dot3(nrm[f], t) > 0.0) inside = 0;
+          }
+          if (inside) acc[p] += q;
+        }
+      }
+    }
+  }
+  memset(out, 0, sizeof(double) * (P > 0 ? P : 1));
+  for (int t = 0; t < T; ++t)
+    for (long p = 0; p < P; ++p) out[p] += bufs[(size_t)t * (P > 0 ? P : 1) + p];
+  free(bufs);
+  return ORC_OK;
+}

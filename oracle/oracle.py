@@ -93,6 +93,8 @@ def _load():
         lib.orc_render_soup.restype = C.c_int
         lib.orc_resample.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, dp, C.c_int]
         lib.orc_resample.restype = C.c_int
+        lib.orc_point_density.argtypes = [dp, C.c_int, C.c_double, C.c_double, dp, C.c_long, C.c_int, dp, C.c_int]
+        lib.orc_point_density.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -230,3 +232,20 @@ def resample(pos, N: int, n: int, weight: str = "density", box: float = 1.0, tot
     if rc != 0:
         raise RuntimeError(f"oracle resample failed with code {rc}")
     return out
+
+
+def point_density(pos, N: int, points, weight: str = "density", box: float = 1.0, total_mass: float = 1.0,
+                  nthreads: int = 0) -> np.ndarray:
+    """Sum over the tetrahedra containing each point (Sec. 3.2, Eq. 4) of rho
+    (weight "density": the total density) or 1 (weight "streams": the
+    number of streams). points: [P][3] in box coordinates."""
+    lib = _load()
+    p = _pos64(pos, N)
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 3))
+    w = {"density": 0, "streams": 1}[weight]
+    out = np.zeros(max(1, pts.shape[0]), dtype=np.float64)
+    rc = lib.orc_point_density(_ptr(p, C.c_double), N, box, total_mass, _ptr(pts, C.c_double), pts.shape[0], w,
+                               _ptr(out, C.c_double), nthreads)
+    if rc != 0:
+        raise RuntimeError(f"oracle point_density failed with code {rc}")
+    return out[:pts.shape[0]]

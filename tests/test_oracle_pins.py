@@ -428,3 +428,58 @@ def test_resample_matches_bruteforce_barycentric():
         a = oracle.resample(pos, N, n, weight)
         b = bf.resample_barycentric(pos, N, n, weight)
         np.testing.assert_allclose(a, b, atol=1e-12 * max(1.0, b.max()))
+
+
+def test_point_density_uniform_and_pancake_closed_form():
+    """Total density and stream count at points (Sec. 3.2, Eq. 4): one stream
+    of density 1 for the unperturbed lattice; for the z-pancake, every stream
+    k whose z-interval holds the point adds h / |z_{k+1} - z_k|."""
+    rng = np.random.default_rng(17)
+    pts = rng.random((300, 3))
+    N = 4
+    idx = np.arange(N ** 3)
+    flat = np.zeros((N ** 3, 4))
+    flat[:, 0], flat[:, 1], flat[:, 2] = idx % N / N, (idx // N) % N / N, idx // (N * N) / N
+    np.testing.assert_allclose(oracle.point_density(flat, N, pts, "density"), 1.0, atol=1e-12)
+    np.testing.assert_allclose(oracle.point_density(flat, N, pts, "streams"), 1.0, atol=0)
+    N, A = 8, 1.6
+    h = 1.0 / N
+    ids = np.arange(N ** 3)
+    i, j, k = ids % N, (ids // N) % N, ids // (N * N)
+    pos = np.zeros((N ** 3, 4))
+    pos[:, 0], pos[:, 1] = i * h, j * h
+    pos[:, 2] = np.mod(k * h - A / (2 * np.pi) * np.sin(2 * np.pi * k * h), 1.0)
+    zk = np.arange(N + 1) * h - A / (2 * np.pi) * np.sin(2 * np.pi * np.arange(N + 1) * h)
+    want_d, want_s = np.zeros(len(pts)), np.zeros(len(pts))
+    for q in range(N):
+        lo, hi = sorted((zk[q], zk[q + 1]))
+        for p, z in enumerate(pts[:, 2]):
+            zz = z - np.floor(z - lo)  # the copy in [lo, lo + 1)
+            if zz <= hi:
+                want_d[p] += h / (hi - lo)
+                want_s[p] += 1
+    assert want_s.max() >= 3
+    np.testing.assert_allclose(oracle.point_density(pos, N, pts, "density"), want_d, rtol=1e-12)
+    np.testing.assert_allclose(oracle.point_density(pos, N, pts, "streams"), want_s, atol=0)
+
+
+def test_point_density_matches_bruteforce_barycentric():
+    """Against an independent barycentric inside test over all periodic
+    copies of every tetrahedron."""
+    N = 3
+    pos = ZeldovichField.generate(N, -2.0, 1.5, 11).positions(1.3).astype(np.float64)
+    verts, rho, _ = bf.lattice_tets(pos, N)
+    pts = np.random.default_rng(5).random((200, 3))
+    want_d, want_s = np.zeros(len(pts)), np.zeros(len(pts))
+    shifts = np.array([[a, b, c] for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)], dtype=np.float64)
+    for t in range(verts.shape[0]):
+        if rho[t] == 0.0:
+            continue
+        Minv = np.linalg.inv(np.vstack([verts[t].T, np.ones(4)]))
+        for sh in shifts:
+            lam = Minv @ np.vstack([(pts + sh).T, np.ones(len(pts))])
+            inside = (lam >= 0).all(axis=0)
+            want_d[inside] += rho[t]
+            want_s[inside] += 1
+    np.testing.assert_allclose(oracle.point_density(pos, N, pts, "density"), want_d, rtol=1e-10)
+    np.testing.assert_allclose(oracle.point_density(pos, N, pts, "streams"), want_s, atol=0)
