@@ -25,7 +25,9 @@
 //
 // Both are exact rewritings of rho * dl (no approximation); the volume is
 // never divided by, which keeps sheet-like tetrahedra at caustics well
-// conditioned in FP32.
+// conditioned in FP32. The form has a finite limit as V -> 0 (a sheet of the
+// same mass), so tetrahedra with V == 0 exactly, which contribute nothing,
+// are skipped explicitly through the build pass's zero-volume mask.
 #pragma once
 
 #include <cuda_runtime.h>
