@@ -483,3 +483,27 @@ def test_point_density_matches_bruteforce_barycentric():
             want_s[inside] += 1
     np.testing.assert_allclose(oracle.point_density(pos, N, pts, "density"), want_d, rtol=1e-10)
     np.testing.assert_allclose(oracle.point_density(pos, N, pts, "streams"), want_s, atol=0)
+
+
+@pytest.mark.parametrize("seed", [101, 202, 303, 404])
+def test_oracle_matches_bruteforce_random_views(seed):
+    """Seeded random lattices and views (orthographic in a random direction,
+    or perspective from a random eye outside the box) against the
+    barycentric brute force."""
+    rng = np.random.default_rng(seed)
+    N = 3
+    pos = ZeldovichField.generate(N, -2.0, 1.5, seed).positions(float(rng.uniform(0.5, 2.0)))
+    if seed % 2:
+        fwd = rng.normal(size=3)
+        fwd[2] = abs(fwd[2]) + 0.5
+        cam = camera_dict("ortho", 20, 17, fwd=fwd, up=(0, 1, 0), lo=(-0.4, -0.4), hi=(1.4, 1.4), wrap=False)
+    else:
+        d = rng.normal(size=3)
+        eye = np.array([0.5, 0.5, 0.5]) + 2.2 * d / np.linalg.norm(d)
+        target = np.array([0.5, 0.5, 0.5]) + rng.uniform(-0.1, 0.1, 3)
+        up = (0, 0, 1) if abs((target - eye)[2]) < 0.9 * np.linalg.norm(target - eye) else (0, 1, 0)
+        cam = camera_dict("persp", 19, 16, eye=eye, fwd=target - eye, up=up, fov_y_deg=50.0)
+    a = oracle.render(pos, N, cam)
+    b = bf.render_barycentric(pos, N, cam)
+    assert a.max() > 0
+    np.testing.assert_allclose(a, b, atol=1e-11 * a.max())
