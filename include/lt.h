@@ -63,7 +63,8 @@ typedef enum {
   LT_ERR_BEHIND_EYE = 5,  /* a cube straddles the eye plane of a perspective frame */
   LT_ERR_RANGE = 6,       /* a pixel exceeded the fixed-point accumulator range */
   LT_ERR_STATE = 7,       /* calls made out of order (e.g. render before bin) */
-  LT_ERR_NOMEM = 8        /* device allocation failed */
+  LT_ERR_NOMEM = 8,       /* device allocation failed */
+  LT_ERR_BOUNDS = 9       /* an index check failed (only in a build with LT_CHECK_BOUNDS) */
 } lt_status;
 
 typedef enum { LT_POS_F32X4 = 0, LT_POS_F16_OFFSETS = 1 } lt_pos_format;

@@ -66,5 +66,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+    # --check-bounds: the debugging build whose index checks latch
+    # LT_ERR_BOUNDS instead of touching memory out of range
+    flags = (["-Xptxas", "-v"] if "--ptxas" in sys.argv else []) + \
+        (["-DLT_CHECK_BOUNDS"] if "--check-bounds" in sys.argv else [])
+    print(build(force="--force" in sys.argv or "--check-bounds" in sys.argv, verbose="-v" in sys.argv,
+                extra_flags=flags or None))

@@ -64,6 +64,7 @@ STATUS = {
     6: "LT_ERR_RANGE",
     7: "LT_ERR_STATE",
     8: "LT_ERR_NOMEM",
+    9: "LT_ERR_BOUNDS",
 }
 
 # every symbol declared in include/lt.h

@@ -290,6 +290,7 @@ lt_status take_device_errors(lt_ctx* ctx) {
   if (e & lt::kErrCapacity) return LT_ERR_CAPACITY;
   if (e & lt::kErrBehindEye) return LT_ERR_BEHIND_EYE;
   if (e & lt::kErrRange) return LT_ERR_RANGE;
+  if (e & lt::kErrBounds) return LT_ERR_BOUNDS;
   return LT_OK;
 }
 
@@ -433,6 +434,7 @@ const char* lt_status_str(lt_status s) {
     case LT_ERR_RANGE: return "fixed-point accumulator range exceeded";
     case LT_ERR_STATE: return "calls made out of order";
     case LT_ERR_NOMEM: return "device allocation failed";
+    case LT_ERR_BOUNDS: return "index check failed (bounds-checking build)";
   }
   return "unknown status";
 }

@@ -53,6 +53,7 @@ enum : unsigned {
   kErrNonFinite = 2u,
   kErrBehindEye = 4u,
   kErrRange = 8u,
+  kErrBounds = 16u,  // an index check of a build with LT_CHECK_BOUNDS failed
 };
 
 // Device counters, one block of them per context.
@@ -102,6 +103,15 @@ __device__ __forceinline__ unsigned div_n(const Lattice& L, unsigned n) {
   const unsigned t = __umulhi(L.div_m, n);
   return (t + ((n - t) >> L.div_s1)) >> L.div_s2;
 }
+
+// Index checks of a debugging build (compiled with -DLT_CHECK_BOUNDS): a
+// failed check latches kErrBounds and the access is skipped; the default
+// build compiles them away.
+#ifdef LT_CHECK_BOUNDS
+#define LT_IN_BOUNDS(cond, err) ((cond) ? true : (atomicOr((err), kErrBounds), false))
+#else
+#define LT_IN_BOUNDS(cond, err) true
+#endif
 
 // True when tetrahedron s of `cube` in snapshot `snap` has zero volume.
 __device__ __forceinline__ bool tet_degenerate(const Lattice& L, int snap, long long cube, int s) {

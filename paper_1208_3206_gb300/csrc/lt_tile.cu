@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
       bool ok = false;
       if (tau < ntet) {
         const unsigned rel = cr + (unsigned)lane;  // < 38
-        const long long cube = (long long)a.list[e0 + cq + rel / 6u];
+        const unsigned long long li = e0 + cq + rel / 6u;
+        const long long cube = LT_IN_BOUNDS(li < e1, &a.ctr->errors) ? (long long)a.list[li] : 0;
         const int s = (int)(rel % 6u);
         const bool zero_volume = tet_degenerate(a.L, F.snapshot, cube, s);  // load issued alongside the vertices
         ok = persp ? project_tet<true>(a.L, F, cube, s, P) : project_tet<false>(a.L, F, cube, s, P);
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
         const int slot = __popc(__ballot_sync(FULL, nrows > 0) & lt_mask);
         int rtotal;
         const int roff = warp_excl_scan(nrows, rtotal);
-        if (nrows > 0) {
+        if (nrows > 0 && LT_IN_BOUNDS(slot < 32, &a.ctr->errors)) {
           float4* R = reinterpret_cast<float4*>(recs + slot * kRec);
           const bool flagged = may_need_exact(t, sig, delta);
           const bool whole_rows = may_miss_fragments(t, sig, delta);
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
           int ptotal;
           const int poff = warp_excl_scan(len, ptotal);
           const int jslot = __popc(__ballot_sync(FULL, len > 0) & lt_mask);
-          if (len > 0) jobs[jslot] = make_int4(xa, Yr, o, poff);
+          if (len > 0 && LT_IN_BOUNDS(jslot < 32 && o < 32, &a.ctr->errors)) jobs[jslot] = make_int4(xa, Yr, o, poff);
           __syncwarp();
           // ---- 4. walk the pixels of the jobs, 32 per step
           int pprev = 0;
@@ -313,7 +314,8 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
                   exact = fragment_needs_exact(f0, f1, f2, f3, ra, rbv, R[7], R[8].w, q * q, v, sig);
                 }
                 if (!exact) {
-                  if (v > 0.0f) accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], v, &a.ctr->errors);
+                  if (v > 0.0f && LT_IN_BOUNDS(X >= 0 && X < tw && Y >= 0 && Y < th, &a.ctr->errors))
+                    accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], v, &a.ctr->errors);
                 } else {
                   const float4 r8 = R[8];
                   qent = pack_frag((unsigned)(tb + __float_as_int(r8.z)), __float_as_int(r8.x), __float_as_int(r8.y),
@@ -371,7 +373,9 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
       const unsigned tau_o = (unsigned)(q & 0xffffffffull);
       const int sxo = (int)((q >> 32) & 127u) - 64, syo = (int)((q >> 39) & 127u) - 64;
       const int X = (int)((q >> 46) & 63u), Y = (int)((q >> 52) & 63u);
-      const long long cube = (long long)a.list[e0 + (unsigned long long)(tau_o / 6)];
+      const unsigned long long li = e0 + (unsigned long long)(tau_o / 6);
+      if (!LT_IN_BOUNDS(li < e1 && X < tw && Y < th, &a.ctr->errors)) continue;
+      const long long cube = (long long)a.list[li];
       const double val = exact_fragment(a.L, F, cube, (int)(tau_o % 6), sxo, syo, tx0 + X, ty0 + Y, F.m_tet);
       if (val > 0.0) accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], (float)(val / F.unit), &a.ctr->errors);
     }

@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_status_strings_and_null_arguments(lib):
-    for code in range(9):
+    for code in range(10):
         assert lib.lt_status_str(code)
     assert lib.lt_status_str(99) == b"unknown status"
     # argument checks happen before any CUDA call
@@ -74,3 +74,15 @@ def test_frame_mass_static_argument_checks(lib):
     assert lib.lt_frame_mass_static(fake, 1, 4, 4, 0.0, fake, None) == 1
     assert lib.lt_frame_mass_static(fake, 1, 4, 4, float("nan"), fake, None) == 1
     assert lib.lt_frame_mass_static(fake, 129, 4, 4, 1.0, fake, None) == 3
+
+
+def test_bounds_checking_build_compiles(tmp_path):
+    """The debugging build with index checks (LT_CHECK_BOUNDS) stays
+    compilable (compile only; the checks latch LT_ERR_BOUNDS when run)."""
+    import subprocess
+    from paper_1208_3206_gb300 import _build
+    src = os.path.join(_build.CSRC, "lt_tile.cu")
+    cmd = [_build._nvcc(), *_build.ARCH, *_build.FLAGS, "-DLT_CHECK_BOUNDS", "-c", src, "-o",
+           str(tmp_path / "lt_tile_checked.o")]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
