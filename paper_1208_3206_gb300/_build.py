@@ -28,8 +28,14 @@ def _nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def _stale() -> bool:
+STAMP = os.path.join(OUT_DIR, "flags.txt")  # the extra flags the library was built with
+
+
+def _stale(extra) -> bool:
     if not os.path.exists(LIB):
+        return True
+    built_with = open(STAMP).read() if os.path.exists(STAMP) else None
+    if built_with != " ".join(extra):
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS] + [os.path.join(INCLUDE, "lt.h")]
@@ -37,8 +43,9 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile liblt.so if missing or older than its sources; returns its path."""
-    if not force and not _stale():
+    """Compile liblt.so if missing, older than its sources or built with
+    other extra flags (a bounds-checking build, say); returns its path."""
+    if not force and not _stale(list(extra_flags or [])):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
@@ -62,6 +69,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(" ".join(extra))
     return LIB
 
 
