@@ -293,8 +293,7 @@ def run_lt(args, rank: int, world: int):
     props = tc.get_device_properties(dev)
     sms = props.multi_processor_count
     flops_per_frag = FLOPS_PER_FRAGMENT_PERSP if persp else FLOPS_PER_FRAGMENT_ORTHO
-    peak_clock_mhz = 2070.0
-    peak = sms * 128 * 2 * peak_clock_mhz * 1e6 / 1e12  # TFLOP/s FP32 at the maximum SM clock
+    peak, peak_clock_mhz, clock_src = fp32_peak_tflops(sms)
     achieved = total_frags * flops_per_frag / (raster_ms * 1e-3) / 1e12
 
     value = world * total_frags / (ms * 1e-3)
@@ -337,7 +336,7 @@ def run_lt(args, rank: int, world: int):
             "frac": achieved / peak,
             "traffic": None,
             "counted": f"{flops_per_frag} FP32 flops per fragment",
-            "peak_from": f"{sms} SMs x 128 FP32 lanes x 2 x {peak_clock_mhz:.0f} MHz",
+            "peak_from": f"{sms} SMs x 128 FP32 lanes x 2 x {peak_clock_mhz:.0f} MHz ({clock_src})",
             "raster_ms": raster_ms,
         },
         "e2e": {
@@ -359,6 +358,22 @@ def run_lt(args, rank: int, world: int):
 
 # ---------------------------------------------------------------------------
 # CPU oracle
+
+
+def fp32_peak_tflops(sms: int):
+    """FP32 peak for the ALU roofline: SMs x 128 lanes x 2 flops x the
+    maximum SM clock, read from MEASURED_PEAKS.json when it is there (else
+    GB300's 2070 MHz). Returns (TFLOP/s, MHz, where the clock came from)."""
+    mhz, src = 2070.0, "GB300 maximum SM clock"
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = float(json.load(fh).get("sm_max_mhz") or 0.0)
+        if v > 0:
+            mhz, src = v, "sm_max_mhz of MEASURED_PEAKS.json"
+    except (OSError, ValueError):
+        pass
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, mhz, src
 
 
 def central_crop(cam, crop: int):

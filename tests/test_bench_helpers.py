@@ -41,3 +41,9 @@ def test_reference_arm_json_line():
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["config"]["workload"] == "zel32_ortho256"
+
+
+def test_fp32_peak_from_unit_counts_and_clock():
+    peak, mhz, src = bench.fp32_peak_tflops(152)
+    assert mhz > 0 and src
+    assert abs(peak - 152 * 128 * 2 * mhz * 1e-6) < 1e-9
