@@ -87,6 +87,15 @@ def lib_path() -> str:
     return _build.LIB
 
 
+def build_flags() -> str:
+    """Extra compiler flags liblt.so was built with ("" for the default build)."""
+    try:
+        with open(_build.STAMP) as fh:
+            return fh.read().strip()
+    except OSError:
+        return ""
+
+
 def load(build_if_missing: bool = False):
     """Load liblt.so. Raises if it has not been built (no CPU fallback exists)."""
     global _lib
@@ -99,6 +108,11 @@ def load(build_if_missing: bool = False):
         else:
             raise RuntimeError(
                 f"liblt.so not found at {path}: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+    flags = build_flags()
+    if flags and os.environ.get("LT_ALLOW_DEBUG_BUILD") != "1":
+        # a debugging build (bounds checks, ptxas report) must not be timed
+        # or tested by mistake: rebuild the default one
+        _build.build(force=True)
     lib = C.CDLL(path)
     vp, ip, fp, dp = C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_double)
     cam_p = C.POINTER(LtCamera)

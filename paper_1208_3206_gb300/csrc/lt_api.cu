@@ -603,8 +603,9 @@ lt_status lt_count_fragments(lt_ctx* ctx, long long* h_counts, lt_stream stream)
 lt_status lt_render_backward(lt_ctx* ctx, const float* d_dL_dimage, float* d_dL_dpos, lt_stream stream) {
   if (!ctx || !d_dL_dimage || !d_dL_dpos) return LT_ERR_ARG;
   if (!ctx->binned) return LT_ERR_STATE;
-  for (int f = 0; f < ctx->n_frames; ++f)
-    if (ctx->h_frames[f].persp) return LT_ERR_ARG;  // adjoint of orthographic views only
+  // adjoint of orthographic views only; any_persp describes the frames of the
+  // last bin (the pinned staging of h_frames is reused by lt_render_atomic)
+  if (ctx->any_persp) return LT_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n = (size_t)ctx->n_snap * ctx->L.n_particles * 24;
   lt_status st = grow(&ctx->d_corner_grad, &ctx->corner_grad_cap, n);

@@ -507,3 +507,33 @@ def test_oracle_matches_bruteforce_random_views(seed):
     b = bf.render_barycentric(pos, N, cam)
     assert a.max() > 0
     np.testing.assert_allclose(a, b, atol=1e-11 * a.max())
+
+
+@pytest.mark.parametrize("view", ["ortho_wrap", "persp"])
+def test_render_crops_equal_slices_of_the_full_frame(view):
+    """Several offset crops in one call (including ones that touch the frame
+    edges and overlap each other) equal the same slices of the full-frame
+    render: pins the crop offsets and the per-crop output layout that the
+    sampled parity tests and the benchmark's CPU leg rely on."""
+    N = 8
+    pos = ZeldovichField.generate(N, -2.0, 3.0, 77).positions(1.7)
+    if view == "ortho_wrap":
+        cam = camera_dict("ortho", 61, 47, fwd=(0.2, -0.1, 1.0), up=(0, 1, 0), lo=(0.05, -0.1), hi=(1.05, 0.9),
+                          wrap=True)
+    else:
+        cam = camera_dict("persp", 58, 64, eye=(0.5, -1.3, 0.9), fwd=(0.0, 1.8, -0.4), up=(0, 0, 1), fov_y_deg=55)
+    full, nf_full, _ = oracle.render(pos, N, cam, return_counts=True)
+    crops = [(0, 0, 61 if view == "ortho_wrap" else 58, 1), (3, 5, 17, 9), (40, 30, 18, 17), (10, 8, 21, 23),
+             (0, 20, 7, 27), (33, 0, 1, 1)]
+    imgs, nf, _ = oracle.render_crops(pos, N, cam, crops)
+    assert len(imgs) == len(crops)
+    for (x, y, w, h), got in zip(crops, imgs):
+        assert got.shape == (h, w)
+        np.testing.assert_array_equal(got, full[y:y + h, x:x + w])
+    # fragments are counted per crop: the batched count is the sum of the
+    # crops' own counts (overlapping crops count their shared pixels twice)
+    assert nf == sum(oracle.render_crops(pos, N, cam, [c])[1] for c in crops)
+    assert 0 < nf
+    single, nf_one, _ = oracle.render_crops(pos, N, cam, [(0, 0, cam["W"], cam["H"])])
+    np.testing.assert_array_equal(single[0], full)
+    assert nf_one == nf_full
