@@ -163,8 +163,12 @@ def run_lt(args, rank: int, world: int):
 
     R = Renderer()
     pos = torch.from_numpy(pos_np).to(dev)
-    R.build_tets(pos, N)
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record()
+    R.build_tets(pos, N)  # volumes, densities and zero-volume masks of every snapshot
+    q1.record()
     R.sync()
+    build_ms = q0.elapsed_time(q1)
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         # autotune the tile size and CTA shape on a subset of the frames
@@ -210,9 +214,14 @@ def run_lt(args, rank: int, world: int):
     log(f"timed: {ms:.1f} ms per step")
     R.sync()
 
-    # raster kernel alone (the dominant kernel), timed with events on its stream
+    # raster kernel alone (the dominant kernel), timed with events on its
+    # stream; the project-and-bin pass before it is timed too (it includes one
+    # host synchronisation, to size the lists)
     with torch.cuda.stream(stream):
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
         R.project_bin(cams, snaps)
+        p1.record(stream)
         R.render_tiles(image=img)
         stream.synchronize()
         r0 = torch.cuda.Event(enable_timing=True)
@@ -224,29 +233,16 @@ def run_lt(args, rank: int, world: int):
         r1.record(stream)
         stream.synchronize()
     raster_ms = r0.elapsed_time(r1) / reps
+    bin_ms = p0.elapsed_time(p1)
     R.sync()
 
-    # end to end through the public API: pinned host positions in, images out
+    # end to end through the public API: pinned host positions in, images out,
+    # pipelined per snapshot (see e2e_pipelined)
     host_pos = torch.from_numpy(pos_np).pin_memory()
     host_img = torch.empty((F, H, W), dtype=torch.float32).pin_memory()
     e2e_steps = max(2, min(args.steps, 3))
-    with torch.cuda.stream(stream):
-        pos.copy_(host_pos, non_blocking=True)
-        R.graph_launch(stream)
-        host_img.copy_(img, non_blocking=True)
-        stream.synchronize()
-        barrier()
-        x0 = torch.cuda.Event(enable_timing=True)
-        x1 = torch.cuda.Event(enable_timing=True)
-        x0.record(stream)
-        for _ in range(e2e_steps):
-            pos.copy_(host_pos, non_blocking=True)
-            R.graph_launch(stream)
-            host_img.copy_(img, non_blocking=True)
-        x1.record(stream)
-        stream.synchronize()
-    e2e_ms = x0.elapsed_time(x1) / e2e_steps
-    R.sync()
+    e2e_ms = e2e_pipelined(pos, host_pos, img, host_img, N, cams, snaps, best, e2e_steps, barrier)
+    log(f"end to end: {e2e_ms:.1f} ms per step")
 
     # plain one-cube-per-thread atomic form (same per-tetrahedron arithmetic and
     # the same exact path) on every 8th frame, against the tiled form on the
@@ -334,10 +330,17 @@ def run_lt(args, rank: int, world: int):
             "peak": peak,
             "unit": "TFLOP/s",
             "frac": achieved / peak,
-            "traffic": None,
+            "traffic": raster_traffic(F),
             "counted": f"{flops_per_frag} FP32 flops per fragment",
             "peak_from": f"{sms} SMs x 128 FP32 lanes x 2 x {peak_clock_mhz:.0f} MHz ({clock_src})",
             "raster_ms": raster_ms,
+        },
+        "passes": {
+            "build_ms": build_ms,
+            "build": "lt_build_tets of all snapshots, once per set of positions (outside the step)",
+            "bin_ms_per_step": bin_ms,
+            "raster_ms_per_step": raster_ms,
+            "step_ms": ms,
         },
         "e2e": {
             "value": world * total_frags / (e2e_ms * 1e-3),
@@ -356,8 +359,95 @@ def run_lt(args, rank: int, world: int):
     return line, (c, pos_np, cams, snaps, gpu_crop)
 
 
+def e2e_pipelined(pos, host_pos, img, host_img, N, cams, snaps, cfg, steps, barrier):
+    """Milliseconds per step of the whole job through the public API with
+    host buffers: every step copies all snapshots' positions in from pinned
+    host memory and every frame's image out to it. One Renderer (context)
+    and one graph per snapshot, over that snapshot's slice of the device
+    positions and its frames' slice of the device images; three streams, so
+    that the copy in of snapshot s + 1 and the copy out of snapshot s - 1 run
+    under the render of snapshot s. A snapshot's copy in waits for its
+    previous render (which reads the positions), and its render waits for
+    its previous copy out (which reads the images)."""
+    import torch
+
+    from paper_1208_3206_gb300.render import Renderer
+
+    groups = sorted(set(snaps))
+    copy_in, compute, copy_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    parts = []
+    for g in groups:
+        fr = [q for q in range(len(cams)) if snaps[q] == g]
+        lo, hi = fr[0], fr[-1] + 1
+        assert fr == list(range(lo, hi)), "frames of a snapshot must be contiguous"
+        Rg = Renderer(tile=cfg.get("tile", 0), raster_threads=cfg.get("raster_threads", 0))
+        Rg.build_tets(pos[g], N)
+        with torch.cuda.stream(compute):
+            Rg.graph_build(cams[lo:hi], None, image=img[lo:hi], stream=compute)
+            Rg.sync()
+        ev = {k: torch.cuda.Event() for k in ("in", "done", "out")}
+        parts.append((g, lo, hi, Rg, ev))
+    torch.cuda.synchronize()
+
+    def one_step():
+        for g, lo, hi, Rg, ev in parts:
+            copy_in.wait_event(ev["done"])
+            with torch.cuda.stream(copy_in):
+                pos[g].copy_(host_pos[g], non_blocking=True)
+            ev["in"].record(copy_in)
+            compute.wait_event(ev["in"])
+            compute.wait_event(ev["out"])
+            Rg.graph_launch(compute)
+            ev["done"].record(compute)
+            copy_out.wait_event(ev["done"])
+            with torch.cuda.stream(copy_out):
+                host_img[lo:hi].copy_(img[lo:hi], non_blocking=True)
+            ev["out"].record(copy_out)
+
+    one_step()  # warm-up
+    torch.cuda.synchronize()
+    barrier()
+    x0 = torch.cuda.Event(enable_timing=True)
+    x1 = torch.cuda.Event(enable_timing=True)
+    x0.record(copy_in)
+    for _ in range(steps):
+        one_step()
+    x1.record(copy_out)
+    torch.cuda.synchronize()
+    for _, _, _, Rg, _ in parts:
+        Rg.sync()
+        Rg.close()
+    return x0.elapsed_time(x1) / steps
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle
+
+
+# DRAM bytes (read + write) of one k_tile launch per frame of the headline
+# workload, from an ncu capture of the kernel built from the sources whose
+# hash is recorded with it; None when the raster has changed since.
+RASTER_TRAFFIC = {"bytes_per_frame": None, "sources_sha16": None, "capture": None}
+
+
+def raster_sources_sha16() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("lt_tile.cu", "lt_common.cuh"):
+        with open(os.path.join(ROOT, "paper_1208_3206_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def raster_traffic(frames: int):
+    """Measured DRAM bytes of one raster launch over `frames` frames (the
+    per-frame capture scaled by the frames), or None when the capture is
+    missing or older than the raster's sources."""
+    t = RASTER_TRAFFIC
+    if not t["bytes_per_frame"] or t["sources_sha16"] != raster_sources_sha16():
+        return None
+    return t["bytes_per_frame"] * frames
 
 
 def fp32_peak_tflops(sms: int):

@@ -61,7 +61,7 @@ typedef enum {
   LT_ERR_CAPACITY = 3,    /* a bin list outgrew its reserved capacity */
   LT_ERR_NONFINITE = 4,   /* a particle position is NaN or infinite */
   LT_ERR_BEHIND_EYE = 5,  /* a cube straddles the eye plane of a perspective frame */
-  LT_ERR_RANGE = 6,       /* a pixel exceeded the fixed-point accumulator range */
+  LT_ERR_RANGE = 6,       /* a pixel exceeded the 64-bit fixed-point accumulator range (see frac_bits) */
   LT_ERR_STATE = 7,       /* calls made out of order (e.g. render before bin) */
   LT_ERR_NOMEM = 8,       /* device allocation failed */
   LT_ERR_BOUNDS = 9       /* an index check failed (only in a build with LT_CHECK_BOUNDS) */
@@ -98,7 +98,10 @@ typedef struct {
   int tile;           /* screen tile edge in pixels: 8, 16, 32 or 64 (default 16) */
   int raster_threads; /* threads per raster CTA: 64..256, multiple of 32 (default 256) */
   int ctas_per_sm;    /* persistent raster CTAs per SM (default: occupancy limit) */
-  int frac_bits;      /* fixed-point fraction bits relative to the mean column density (default 28) */
+  int frac_bits;      /* fixed-point fraction bits relative to the mean column density sigma, 8..62
+                         (default 28): each pixel is summed in a 64-bit integer that resolves
+                         2^-frac_bits sigma and holds values below 2^(64 - frac_bits) sigma; a pixel
+                         that would pass that latches LT_ERR_RANGE */
 } lt_config;
 
 typedef struct {
@@ -224,7 +227,11 @@ lt_status lt_render_backward(lt_ctx* ctx, const float* d_dL_dimage, float* d_dL_
  * size the bins (reserving 25 % headroom), then captures on `stream`.
  * Replays re-read the registered positions, so new snapshot contents
  * (same shape) may be written between launches. Capacity overflow during a
- * replay latches LT_ERR_CAPACITY.
+ * replay latches LT_ERR_CAPACITY. The graph keeps its own copy of its
+ * frames: direct calls made after lt_graph_build do not change its views.
+ * A later lt_build_tets, or a direct call that has to reallocate a buffer
+ * the graph uses (more frames or tiles, longer lists), makes the graph stale:
+ * lt_graph_launch then returns LT_ERR_STATE until lt_graph_build runs again.
  */
 lt_status lt_graph_build(lt_ctx* ctx, const lt_camera* cams, int n_frames, const int* frame_snapshot,
                          float* d_image, double* d_mass, lt_stream stream);

@@ -51,6 +51,8 @@ struct lt_ctx {
   unsigned long long list_cap = 0;
   unsigned long long entries = 0;
   unsigned* d_hist = nullptr;
+  unsigned* d_desc = nullptr;  // per (frame, cube) tile descriptors of the bin pass (null above the budget)
+  size_t desc_cap = 0;
   bool binned = false;
   // counters
   DevCounters* d_ctr = nullptr;
@@ -68,6 +70,11 @@ struct lt_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_kernels = 0;
+  FrameDev* d_frames_graph = nullptr;  // the graph's own copy of its frames
+  size_t frames_graph_cap = 0;
+  // set when a buffer the graph captured is reallocated or the lattice is
+  // registered again: lt_graph_launch then refuses to replay
+  bool graph_stale = false;
   // host-side latched error
   lt_status latched = LT_OK;
 };
@@ -83,6 +90,8 @@ namespace {
     }                                                  \
   } while (0)
 
+constexpr size_t kDescBudgetBytes = (size_t)16 << 30;  // tile descriptors kept up to 16 GiB
+
 lt_config default_config() {
   lt_config c;
   c.tile = 16;
@@ -97,7 +106,7 @@ bool valid_config(const lt_config& c) {
   const bool thr_ok = c.raster_threads == 0 || (c.raster_threads >= 64 && c.raster_threads <= 256 &&
                                                 c.raster_threads % 32 == 0);
   const bool cps_ok = c.ctas_per_sm >= 0 && c.ctas_per_sm <= 32;
-  const bool fb_ok = c.frac_bits == 0 || (c.frac_bits >= 8 && c.frac_bits <= 40);
+  const bool fb_ok = c.frac_bits == 0 || (c.frac_bits >= 8 && c.frac_bits <= 62);
   return tile_ok && thr_ok && cps_ok && fb_ok;
 }
 
@@ -123,6 +132,15 @@ lt_status grow(T** p, size_t* cap, size_t n) {
   }
   *cap = n;
   return LT_OK;
+}
+
+// grow() for a buffer a captured graph may use: a reallocation makes the
+// graph stale (its kernels hold the old address).
+template <typename T>
+lt_status grow_c(lt_ctx* ctx, T** p, size_t* cap, size_t n) {
+  if (*cap >= n && *p) return LT_OK;
+  ctx->graph_stale = true;
+  return grow(p, cap, n);
 }
 
 lt_status grow_pinned(FrameDev** p, size_t* cap, size_t n) {
@@ -317,7 +335,7 @@ lt_status prepare_frames(lt_ctx* ctx, const lt_camera* cams, int n_frames, const
 lt_status bin_launches(lt_ctx* ctx, cudaStream_t s, bool allow_sync) {
   const long long n = ctx->n_tiles;
   LT_CUDA(cudaMemsetAsync(ctx->d_count, 0, sizeof(unsigned) * n, s));
-  LT_CUDA(lt::launch_bin_count(ctx->L, ctx->d_frames, ctx->n_frames, ctx->d_count, ctx->d_ctr, s));
+  LT_CUDA(lt::launch_bin_count(ctx->L, ctx->d_frames, ctx->n_frames, ctx->d_count, ctx->d_desc, ctx->d_ctr, s));
   LT_CUDA(lt::launch_scan(ctx->d_count, n, ctx->d_off, ctx->d_scan_tmp, s));
   if (allow_sync) {
     LT_CUDA(cudaMemcpyAsync(ctx->h_u64, ctx->d_off + n, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -326,14 +344,14 @@ lt_status bin_launches(lt_ctx* ctx, cudaStream_t s, bool allow_sync) {
     ctx->entries = total;
     if (total > ctx->list_cap) {
       size_t cap = ctx->list_cap;
-      lt_status st = grow(&ctx->d_list, &cap, (size_t)(total + total / 8 + 1024));
+      lt_status st = grow_c(ctx, &ctx->d_list, &cap, (size_t)(total + total / 8 + 1024));
       if (st != LT_OK) return st;
       ctx->list_cap = cap;
     }
   }
   LT_CUDA(cudaMemsetAsync(ctx->d_cursor, 0, sizeof(unsigned) * n, s));
   LT_CUDA(lt::launch_bin_scatter(ctx->L, ctx->d_frames, ctx->n_frames, ctx->d_off, ctx->d_cursor, ctx->d_list,
-                                 ctx->list_cap, ctx->d_ctr, s));
+                                 ctx->list_cap, ctx->d_desc, ctx->d_ctr, s));
   LT_CUDA(lt::launch_worklist(ctx->d_off, n, ctx->d_hist, ctx->d_work, s));
   return LT_OK;
 }
@@ -343,21 +361,21 @@ lt_status ensure_tiles(lt_ctx* ctx, long long n) {
   size_t c;
   if ((size_t)n > ctx->tiles_cap) {
     c = 0;
-    if ((st = grow(&ctx->d_count, &c, (size_t)n)) != LT_OK) return st;
+    if ((st = grow_c(ctx, &ctx->d_count, &c, (size_t)n)) != LT_OK) return st;
     c = 0;
-    if ((st = grow(&ctx->d_cursor, &c, (size_t)n)) != LT_OK) return st;
+    if ((st = grow_c(ctx, &ctx->d_cursor, &c, (size_t)n)) != LT_OK) return st;
     c = 0;
-    if ((st = grow(&ctx->d_off, &c, (size_t)n + 1)) != LT_OK) return st;
+    if ((st = grow_c(ctx, &ctx->d_off, &c, (size_t)n + 1)) != LT_OK) return st;
     c = 0;
-    if ((st = grow(&ctx->d_work, &c, (size_t)n)) != LT_OK) return st;
+    if ((st = grow_c(ctx, &ctx->d_work, &c, (size_t)n)) != LT_OK) return st;
     c = 0;
-    if ((st = grow(&ctx->d_mass_tile, &c, (size_t)n)) != LT_OK) return st;
+    if ((st = grow_c(ctx, &ctx->d_mass_tile, &c, (size_t)n)) != LT_OK) return st;
     ctx->tiles_cap = (size_t)n;
   }
   const size_t words = lt::scan_tmp_words(n);
-  if ((st = grow(&ctx->d_scan_tmp, &ctx->scan_tmp_cap, words)) != LT_OK) return st;
+  if ((st = grow_c(ctx, &ctx->d_scan_tmp, &ctx->scan_tmp_cap, words)) != LT_OK) return st;
   const size_t xq = (size_t)ctx->num_sms * lt::kRasterMaxCtasPerSm * lt::kExactQueueCap;
-  if ((st = grow(&ctx->d_xq, &ctx->xq_cap, xq)) != LT_OK) return st;
+  if ((st = grow_c(ctx, &ctx->d_xq, &ctx->xq_cap, xq)) != LT_OK) return st;
   return LT_OK;
 }
 
@@ -374,6 +392,20 @@ lt_status project_bin_impl(lt_ctx* ctx, const lt_camera* cams, int n_frames, con
   const long long tpf = (long long)ctx->h_frames[0].tiles_x * ctx->h_frames[0].tiles_y;
   const long long n_tiles = tpf * n_frames;
   if ((st = ensure_tiles(ctx, n_tiles)) != LT_OK) return st;
+  // tile descriptors of the bin pass: 4 bytes per (frame, cube), kept only
+  // below a memory budget (above it the scatter projects every cube again)
+  const size_t n_desc = (size_t)n_frames * (size_t)ctx->L.n_particles;
+  if (n_desc * sizeof(unsigned) <= kDescBudgetBytes) {
+    if (grow_c(ctx, &ctx->d_desc, &ctx->desc_cap, n_desc) != LT_OK) {
+      ctx->d_desc = nullptr;
+      ctx->desc_cap = 0;
+    }
+  } else if (ctx->d_desc) {
+    ctx->graph_stale = true;
+    cudaFree(ctx->d_desc);
+    ctx->d_desc = nullptr;
+    ctx->desc_cap = 0;
+  }
   LT_CUDA(cudaMemcpyAsync(ctx->d_frames, ctx->h_frames, sizeof(FrameDev) * n_frames, cudaMemcpyHostToDevice, s));
   ctx->n_frames = n_frames;
   ctx->W = W;
@@ -474,6 +506,7 @@ void lt_destroy(lt_ctx* ctx) {
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   cudaFree(ctx->d_frames);
   cudaFree(ctx->d_frames_aux);
+  cudaFree(ctx->d_frames_graph);
   cudaFree(ctx->d_count);
   cudaFree(ctx->d_cursor);
   cudaFree(ctx->d_off);
@@ -483,6 +516,7 @@ void lt_destroy(lt_ctx* ctx) {
   cudaFree(ctx->d_scan_tmp);
   cudaFree(ctx->d_list);
   cudaFree(ctx->d_hist);
+  cudaFree(ctx->d_desc);
   cudaFree(ctx->d_ctr);
   cudaFree(ctx->d_frag);
   cudaFree(ctx->d_corner_grad);
@@ -528,6 +562,7 @@ lt_status lt_build_tets(lt_ctx* ctx, const void* d_pos, int pos_fmt, int N, floa
   if (st != LT_OK) return st;
   L.degen = ctx->d_degen;
   ctx->L = L;
+  ctx->graph_stale = true;  // a graph captured the previous lattice
   ctx->n_snap = n_snapshots;
   ctx->total_mass = total_mass;
   ctx->have_lattice = true;
@@ -630,14 +665,22 @@ lt_status lt_graph_build(lt_ctx* ctx, const lt_camera* cams, int n_frames, const
     if ((st = grow(&ctx->d_list, &cap, (size_t)want)) != LT_OK) return st;
     ctx->list_cap = cap;
   }
+  // the graph keeps its own copy of the frames, so that later direct calls
+  // (which upload theirs into d_frames) leave its views unchanged
+  if ((st = grow(&ctx->d_frames_graph, &ctx->frames_graph_cap, (size_t)n_frames)) != LT_OK) return st;
+  LT_CUDA(cudaMemcpyAsync(ctx->d_frames_graph, ctx->d_frames, sizeof(FrameDev) * n_frames, cudaMemcpyDeviceToDevice,
+                          s));
   LT_CUDA(cudaStreamSynchronize(s));
   if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
   if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+  FrameDev* const direct_frames = ctx->d_frames;
+  ctx->d_frames = ctx->d_frames_graph;
   LT_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   lt_status st2 = bin_launches(ctx, s, false);
   if (st2 == LT_OK) st2 = render_impl(ctx, d_image, d_mass, s);
   cudaGraph_t g = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(s, &g);
+  ctx->d_frames = direct_frames;
   if (st2 != LT_OK) {
     if (g) cudaGraphDestroy(g);
     return st2;
@@ -657,12 +700,13 @@ lt_status lt_graph_build(lt_ctx* ctx, const lt_camera* cams, int n_frames, const
     if (cudaGraphNodeGetType(nodes[q], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++ctx->graph_kernels;
   }
   LT_CUDA(cudaGraphInstantiate(&ctx->graph_exec, g, 0));
+  ctx->graph_stale = false;
   return LT_OK;
 }
 
 lt_status lt_graph_launch(lt_ctx* ctx, lt_stream stream) {
   if (!ctx) return LT_ERR_ARG;
-  if (!ctx->graph_exec) return LT_ERR_STATE;
+  if (!ctx->graph_exec || ctx->graph_stale) return LT_ERR_STATE;
   LT_CUDA(cudaGraphLaunch(ctx->graph_exec, (cudaStream_t)stream));
   return LT_OK;
 }

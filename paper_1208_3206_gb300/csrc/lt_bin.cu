@@ -1,8 +1,9 @@
 // lt_bin.cu -- project-and-bin pass: for every (frame, cube) the screen
 // tiles overlapped by the cube's projected bounding box; warp-aggregated
-// per-tile counts, a device exclusive scan, a scatter of cube ids into
-// per-tile lists, and the (frame, tile) work list ordered by descending
-// list length (bucketed by log2 of the length).
+// per-tile counts (the count pass also keeps each cube's tile rectangle, so
+// the scatter does not project again), a device exclusive scan, a scatter of
+// cube ids into per-tile lists, and the (frame, tile) work list ordered by
+// descending list length (bucketed by log2 of the length).
 #include "lt_internal.h"
 
 namespace lt {
@@ -73,20 +74,60 @@ __device__ __forceinline__ long long cube_tile_at(const CubeTiles& ct, const Fra
   return F.tile_base + (long long)ty * F.tiles_x + tx;
 }
 
+// The count pass keeps each (frame, cube)'s tiles as one 32-bit descriptor
+// so that the scatter pass need not project the cube again: first tile x and
+// y (12 bits each, below 4095) and the tile counts minus one (4 bits each).
+// A cube with no tiles, and one whose tiles do not fit the form (two
+// periodic intervals, more than 16 tiles along an axis), get a sentinel;
+// the scatter projects the latter again.
+constexpr unsigned kDescNone = 0xFFFFFFFFu, kDescAgain = 0xFFFFFFFEu;  // both have the y field 0xFFF
+
+__device__ __forceinline__ unsigned encode_tiles(bool have, const CubeTiles& ct) {
+  if (!have) return kDescNone;
+  if (ct.nx != 1 || ct.ny != 1) return kDescAgain;
+  const int cx = ct.xhi[0] - ct.xlo[0] + 1, cy = ct.yhi[0] - ct.ylo[0] + 1;
+  if (ct.xlo[0] >= 4095 || ct.ylo[0] >= 4095 || cx > 16 || cy > 16) return kDescAgain;
+  return (unsigned)ct.xlo[0] | ((unsigned)ct.ylo[0] << 12) | ((unsigned)(cx - 1) << 24) | ((unsigned)(cy - 1) << 28);
+}
+
+__device__ __forceinline__ void decode_tiles(unsigned d, CubeTiles& ct) {
+  ct.nx = ct.ny = 1;
+  ct.xlo[0] = (int)(d & 0xFFFu);
+  ct.ylo[0] = (int)((d >> 12) & 0xFFFu);
+  ct.cntx = (int)((d >> 24) & 15u) + 1;
+  ct.cnty = (int)(d >> 28) + 1;
+  ct.xhi[0] = ct.xlo[0] + ct.cntx - 1;
+  ct.yhi[0] = ct.ylo[0] + ct.cnty - 1;
+}
+
 template <bool SCATTER>
 __global__ void __launch_bounds__(256) k_bin(Lattice L, const FrameDev* __restrict__ frames,
                                              const unsigned long long* __restrict__ off, unsigned* __restrict__ cnt,
                                              unsigned* __restrict__ list, unsigned long long capacity,
-                                             DevCounters* __restrict__ ctr) {
+                                             unsigned* __restrict__ desc, DevCounters* __restrict__ ctr) {
   const FrameDev& F = frames[blockIdx.y];
   const long long ncube = L.n_particles;
   const unsigned lane = threadIdx.x & 31;
+  unsigned* fdesc = desc ? desc + (long long)blockIdx.y * ncube : nullptr;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < ncube; base += (long long)gridDim.x * blockDim.x) {
     const long long cube = base + threadIdx.x;
     CubeTiles ct;
     bool finite_ok = true, behind = false;
     bool have = false;
-    if (cube < ncube) have = cube_tiles(L, F, cube, ct, finite_ok, behind);
+    if (cube < ncube) {
+      if (SCATTER && fdesc) {
+        const unsigned d = fdesc[cube];
+        if (d == kDescAgain) {
+          have = cube_tiles(L, F, cube, ct, finite_ok, behind);
+        } else if (d != kDescNone) {
+          decode_tiles(d, ct);
+          have = true;
+        }
+      } else {
+        have = cube_tiles(L, F, cube, ct, finite_ok, behind);
+        if (!SCATTER && fdesc) fdesc[cube] = encode_tiles(have, ct);
+      }
+    }
     if (!SCATTER) {
       const unsigned nb = __reduce_add_sync(0xffffffffu, behind ? 1u : 0u);
       if (lane == 0 && nb) {
@@ -127,17 +168,17 @@ static unsigned bin_blocks(long long ncube) {
 }
 
 cudaError_t launch_bin_count(const Lattice& L, const FrameDev* d_frames, int n_frames, unsigned* d_count,
-                             DevCounters* ctr, cudaStream_t s) {
+                             unsigned* d_desc, DevCounters* ctr, cudaStream_t s) {
   dim3 grid(bin_blocks(L.n_particles), n_frames);
-  k_bin<false><<<grid, 256, 0, s>>>(L, d_frames, nullptr, d_count, nullptr, 0, ctr);
+  k_bin<false><<<grid, 256, 0, s>>>(L, d_frames, nullptr, d_count, nullptr, 0, d_desc, ctr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bin_scatter(const Lattice& L, const FrameDev* d_frames, int n_frames,
                                const unsigned long long* d_off, unsigned* d_cursor, unsigned* d_list,
-                               unsigned long long capacity, DevCounters* ctr, cudaStream_t s) {
+                               unsigned long long capacity, unsigned* d_desc, DevCounters* ctr, cudaStream_t s) {
   dim3 grid(bin_blocks(L.n_particles), n_frames);
-  k_bin<true><<<grid, 256, 0, s>>>(L, d_frames, d_off, d_cursor, d_list, capacity, ctr);
+  k_bin<true><<<grid, 256, 0, s>>>(L, d_frames, d_off, d_cursor, d_list, capacity, d_desc, ctr);
   return cudaGetLastError();
 }
 

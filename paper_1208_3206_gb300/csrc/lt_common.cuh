@@ -642,27 +642,26 @@ __device__ __forceinline__ void row_span(const TetRaster& t, const float* erow, 
   hi += 1e-3f;
 }
 
-// Split a non-negative accumulator-unit value into the two 32-bit shared
-// counters of a pixel: the low kAccLoBits bits and the rest. Integer sums are
-// exact and associative, so the image does not depend on the order of
-// fragments. The pixel value is (hi << kAccLoBits) + lo; lo cannot wrap
-// before 2^(32 - kAccLoBits) = 262144 fragments land in one pixel.
-constexpr int kAccLoBits = 14;
-
-__device__ __forceinline__ void accum_fixed(unsigned* lo, unsigned* hi, float q, unsigned* err) {
-  if (q < 4294967040.0f) {
-    const unsigned u = __float2uint_rn(q);
+// Add a non-negative value q (accumulator units) to a pixel's 64-bit
+// fixed-point sum in shared memory. Integer sums are exact and associative,
+// so the image does not depend on the order of the adds. A value that cannot
+// be converted (2^63 units or more, or not a number) and an add that carries
+// the sum past 2^64 latch kErrRange and are counted: the atomic returns the
+// sum before the add, so a wrap is seen by the add that causes it.
+__device__ __forceinline__ void accum_fixed(unsigned long long* acc, float q, DevCounters* ctr) {
+  constexpr float k2p63 = 9223372036854775808.0f;
+  if (q < k2p63) {
+    const unsigned long long u = __float2ull_rn(q);
     if (u) {
-      atomicAdd(lo, u & ((1u << kAccLoBits) - 1u));
-      atomicAdd(hi, u >> kAccLoBits);
+      const unsigned long long old = atomicAdd(acc, u);
+      if (old > ~0ull - u) {
+        atomicOr(&ctr->errors, kErrRange);
+        atomicAdd(&ctr->range_overflow, 1ull);
+      }
     }
-  } else {
-    const float qh = q * (1.0f / (float)(1u << kAccLoBits));
-    if (qh < 4294967040.0f) {
-      atomicAdd(hi, __float2uint_rn(qh));
-    } else {
-      atomicOr(err, kErrRange);
-    }
+  } else if (!(q <= 0.0f)) {
+    atomicOr(&ctr->errors, kErrRange);
+    atomicAdd(&ctr->range_overflow, 1ull);
   }
 }
 

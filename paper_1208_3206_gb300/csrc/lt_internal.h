@@ -13,14 +13,16 @@ cudaError_t launch_build_tets(const Lattice& L, int n_snap, double m, float* rho
                               DevCounters* ctr, cudaStream_t s);
 
 // ---- lt_bin.cu
+// d_desc (may be null): per (frame, cube) tile descriptors, written by the
+// count pass and read by the scatter
 cudaError_t launch_bin_count(const Lattice& L, const FrameDev* d_frames, int n_frames, unsigned* d_count,
-                             DevCounters* ctr, cudaStream_t s);
+                             unsigned* d_desc, DevCounters* ctr, cudaStream_t s);
 cudaError_t launch_scan(const unsigned* d_count, long long n, unsigned long long* d_off, unsigned long long* d_tmp,
                         cudaStream_t s);
 size_t scan_tmp_words(long long n);
 cudaError_t launch_bin_scatter(const Lattice& L, const FrameDev* d_frames, int n_frames,
                                const unsigned long long* d_off, unsigned* d_cursor, unsigned* d_list,
-                               unsigned long long capacity, DevCounters* ctr, cudaStream_t s);
+                               unsigned long long capacity, unsigned* d_desc, DevCounters* ctr, cudaStream_t s);
 cudaError_t launch_worklist(const unsigned long long* d_off, long long n_tiles, unsigned* d_hist,
                             unsigned long long* d_work, cudaStream_t s);
 

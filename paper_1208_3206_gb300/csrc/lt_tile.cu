@@ -2,19 +2,24 @@
 // counter built on the same walk).
 //
 // One CTA takes (frame, tile) work items from an atomic counter. For its
-// tile, each warp repeatedly takes 32 tetrahedra (one per lane) of the tile's
-// cube list:
-//   1. every lane projects its tetrahedron and builds its raster form (the
-//      per-tetrahedron setup of lt_common.cuh) in tile pixel coordinates;
-//      the records of the drawable ones are compacted into a per-warp table
-//      in shared memory;
+// tile, each warp repeatedly takes a batch of kCB cubes of the tile's cube
+// list:
+//   0. two lanes per cube project its anchor and its eight corners (four
+//      each) into the warp's corner table in shared memory, so every corner
+//      is projected once per tile whatever the number of tetrahedra sharing
+//      it; then, 32 tetrahedra (one per lane) at a time:
+//   1. every lane reads its tetrahedron's four corners from the table and
+//      builds its raster form (the per-tetrahedron setup of lt_common.cuh)
+//      in tile pixel coordinates; the records of the drawable ones are
+//      compacted into a per-warp table in shared memory;
 //   2. a warp scan flattens the (tetrahedron, row) jobs of their bounding
 //      boxes; 32 jobs at a time, each lane finds the pixel span of its row
 //      where every edge function is >= 0;
 //   3. a second scan flattens the spans' pixels; 32 pixels at a time, each
-//      lane evaluates rho * dl and adds it to the tile's fixed-point
-//      accumulators in shared memory (the owner of a job or pixel is found
-//      from the popcount of the step's start mask, without shared memory);
+//      lane evaluates rho * dl and adds it to the pixel's 64-bit fixed-point
+//      accumulator in shared memory with one integer atomic (the owner of a
+//      job or pixel is found from the popcount of the step's start mask,
+//      without shared memory);
 //   4. fragments whose FP32 value may be off by more than the tolerance are
 //      queued and evaluated exactly in FP64 after the walk.
 // Control flow stays uniform across the warp, so lanes are busy in every
@@ -26,6 +31,19 @@
 namespace lt {
 
 constexpr int kRec = 36;  // words per tetrahedron record (stride 4 mod 32: float4 access is conflict-free)
+constexpr int kCB = 16;          // cubes per warp batch (two lanes each in step 0)
+constexpr int kTB = 6 * kCB;     // their tetrahedra: kTB / 32 rounds of steps 1-3
+constexpr int kCorStride = 9;    // float4 per cube in the corner table (eight corners and a pad)
+
+// Per-warp shared memory.
+struct WarpSmem {
+  float4 cor[kCB * kCorStride];  // corner (x, y, 1/Z - 1/Z_anchor, Z) relative to the cube's anchor
+  float4 anc[kCB];               // anchor pixel coordinate as hi + lo: axh, axl, ayh, ayl
+  float4 cinfo[kCB];             // 1/Z_anchor, perspective uncertainty factor, flags, -
+  float recs[32 * kRec];         // records of the drawable tetrahedra of the current 32
+  int4 jobs[32];                 // (tetrahedron, row) jobs of the current step
+};
+constexpr unsigned kCubeValid = 0x100u;  // cinfo flags: bits 0..5 zero-volume mask, this bit: drawable
 // Ill-conditioned fragments are queued per CTA in global memory (a.xq_cap
 // entries per CTA) and evaluated exactly after the tile's walk.
 
@@ -34,7 +52,8 @@ constexpr int kRec = 36;  // words per tetrahedron record (stride 4 mod 32: floa
 // first row job; [1] a[4]; [2] b[4]; [3] c[4] (edge functions); [4] 1/a[4]
 // (row spans); [5] pa0, pb0, pc0, pa1; [6] pb1, pc1, g (perspective depth
 // planes), exact-check flag; [7] edge steepness st[4]; [8] periodic copy
-// (sx, sy), lane, vertex uncertainty.
+// (sx, sy), tetrahedron index within the tile's list (6 x list position
+// + s), vertex uncertainty.
 
 __device__ __forceinline__ unsigned long long pack_frag(unsigned tau, int sx, int sy, int X, int Y) {
   return (unsigned long long)tau | ((unsigned long long)(unsigned)(sx + 64) << 32) |
@@ -76,14 +95,15 @@ __device__ __forceinline__ int warp_excl_scan(int n, int& total) {
 
 template <bool ANY_PERSP, bool COUNT>
 __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, unsigned long long* __restrict__ counts) {
-  extern __shared__ __align__(16) float smem_f[];
+  extern __shared__ __align__(16) float4 smem4[];
   const int T = a.tile;
+  const int AS = T + 5;  // accumulator row stride: consecutive rows start on different banks
   const int nw = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned* acc_lo = reinterpret_cast<unsigned*>(smem_f);
-  unsigned* acc_hi = acc_lo + T * T;
-  float* recs = reinterpret_cast<float*>(acc_hi + T * T) + warp * 32 * kRec;
-  int4* jobs = reinterpret_cast<int4*>(reinterpret_cast<float*>(acc_hi + T * T) + nw * 32 * kRec) + warp * 32;
+  WarpSmem& S = reinterpret_cast<WarpSmem*>(smem4)[warp];
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(reinterpret_cast<WarpSmem*>(smem4) + nw);
+  float* recs = S.recs;
+  int4* jobs = S.jobs;
   __shared__ unsigned long long item_s;
   __shared__ double mass_w[32];
   __shared__ unsigned qn;
@@ -97,7 +117,7 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
       qn = 0u;
     }
     if (!COUNT)
-      for (int q = threadIdx.x; q < 2 * T * T; q += blockDim.x) acc_lo[q] = 0u;
+      for (int q = threadIdx.x; q < T * AS; q += blockDim.x) acc[q] = 0ull;
     __syncthreads();
     const unsigned long long item = item_s;
     if (item >= (unsigned long long)a.n_items) break;
@@ -119,238 +139,305 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
       e0 = min(e0, a.list_cap);
       e1 = a.list_cap;
     }
-    const long long ntet = 6LL * (long long)(e1 - e0);
+    const long long ncl = (long long)(e1 - e0);
     const bool wrap = (!persp) && F.wrap;
     const float Kn0 = 6.0f * F.K;
     const float sig = F.sigma_units;
+    const long long snap_off = (long long)F.snapshot * a.L.n_particles;
 
-    // tb / 6 and tb % 6 carried along the loop (tb advances by nw * 32)
-    const unsigned step_q = (unsigned)(nw * 32) / 6u, step_r = (unsigned)(nw * 32) % 6u;
-    unsigned long long cq = (unsigned long long)warp * 32u / 6u;
-    unsigned cr = (unsigned)(warp * 32) % 6u;
-    for (long long tb = (long long)warp * 32; tb < ntet; tb += (long long)nw * 32) {
-      // ---- 1. one tetrahedron per lane
-      const long long tau = tb + lane;
-      TetProj P;
-      bool ok = false;
-      if (tau < ntet) {
-        const unsigned rel = cr + (unsigned)lane;  // < 38
-        const unsigned long long li = e0 + cq + rel / 6u;
-        const long long cube = LT_IN_BOUNDS(li < e1, &a.ctr->errors) ? (long long)a.list[li] : 0;
-        const int s = (int)(rel % 6u);
-        const bool zero_volume = tet_degenerate(a.L, F.snapshot, cube, s);  // load issued alongside the vertices
-        ok = persp ? project_tet<true>(a.L, F, cube, s, P) : project_tet<false>(a.L, F, cube, s, P);
-        ok = ok && !zero_volume;
-      }
-      float bx0 = 0.f, bx1 = -1.f, by0 = 0.f, by1 = -1.f;
-      int sx0 = 0, sx1 = -1, sy0 = 0, sy1 = -1;
-      if (ok) {
-        bx0 = fminf(fminf(P.x[0], P.x[1]), fminf(P.x[2], P.x[3]));
-        bx1 = fmaxf(fmaxf(P.x[0], P.x[1]), fmaxf(P.x[2], P.x[3]));
-        by0 = fminf(fminf(P.y[0], P.y[1]), fminf(P.y[2], P.y[3]));
-        by1 = fmaxf(fmaxf(P.y[0], P.y[1]), fmaxf(P.y[2], P.y[3]));
-        const float axa = P.axh + P.axl, aya = P.ayh + P.ayl;
-        shift_range(axa + bx0, axa + bx1, (float)tx0 - 0.5f, (float)(tx0 + tw) - 0.5f, (float)F.W, wrap, sx0, sx1);
-        shift_range(aya + by0, aya + by1, (float)ty0 - 0.5f, (float)(ty0 + th) - 0.5f, (float)F.H, wrap, sy0, sy1);
-        sx1 = min(sx1, sx0 + 63);
-        sy1 = min(sy1, sy0 + 63);
-      }
-      const int ncx = max(0, sx1 - sx0 + 1), ncp = ncx * max(0, sy1 - sy0 + 1);
-      float delta = 0.f;
-      if (ok) {
-        const float Rx = fmaxf(fmaxf(fabsf(P.x[0]), fabsf(P.x[1])), fmaxf(fabsf(P.x[2]), fabsf(P.x[3])));
-        const float Ry = fmaxf(fmaxf(fabsf(P.y[0]), fabsf(P.y[1])), fmaxf(fabsf(P.y[2]), fabsf(P.y[3])));
-        float Rv = fmaxf(Rx, Ry);
-        if (persp) {
-          // the anchor's offset from the view axis times the depth offsets
-          const float dwm = fmaxf(fmaxf(fabsf(P.dw[0]), fabsf(P.dw[1])), fmaxf(fabsf(P.dw[2]), fabsf(P.dw[3])));
-          const float off = fmaxf(fabsf(P.axh - F.cx), fabsf(P.ayh - F.cy));
-          Rv += off * __fdividef(dwm, P.w0);
-        }
-        delta = vertex_uncertainty(Rv, persp);
-      }
-      const float margin = 1e-3f + delta;
-      const int rounds = __reduce_max_sync(FULL, ncp);
-      float Kn = Kn0, invKn = 0.f;
-      if (persp && ok) {
-        Kn = __fdividef(Kn0, P.z[0] * P.z[1] * P.z[2] * P.z[3]);
-        invKn = fast_rcp(Kn);
-      }
-      for (int r = 0; r < rounds; ++r) {
-        int nrows = 0, qx0 = 0, qx1 = 0, qy0 = 0, sx = 0, sy = 0;
-        TetRaster t;
-        if (r < ncp) {
-          sx = sx0 + r % ncx;
-          sy = sy0 + r / ncx;
-          // vertex coordinates relative to the tile origin: anchor + shift - tile corner
-          const float ox = ((float)(tx0 - sx * F.W) - P.axh) - P.axl;
-          const float oy = ((float)(ty0 - sy * F.H) - P.ayh) - P.ayl;
-          const float x0 = P.x[0] - ox, x1 = P.x[1] - ox, x2 = P.x[2] - ox, x3 = P.x[3] - ox;
-          const float y0 = P.y[0] - oy, y1 = P.y[1] - oy, y2 = P.y[2] - oy, y3 = P.y[3] - oy;
-          qx0 = max(0, (int)ceilf(bx0 - ox - margin));
-          qx1 = min(tw - 1, (int)floorf(bx1 - ox + margin));
-          qy0 = max(0, (int)ceilf(by0 - oy - margin));
-          const int qy1 = min(th - 1, (int)floorf(by1 - oy + margin));
-          if (qx0 <= qx1 && qy0 <= qy1) {
-            const bool set =
-                persp ? tet_setup<true>(x0, y0, x1, y1, x2, y2, x3, y3, P.dw[0], P.dw[1], P.dw[2], P.dw[3], Kn,
-                                        P.w0, invKn, t)
-                      : tet_setup<false>(x0, y0, x1, y1, x2, y2, x3, y3, 0.f, 0.f, 0.f, 0.f, Kn, 0.f, 0.f, t);
-            if (set) nrows = qy1 - qy0 + 1;
-          }
-        }
-        // ---- 2. records of the drawable tetrahedra, compacted, and the
-        // flattened (tetrahedron, row) jobs
-        const unsigned lt_mask = (1u << lane) - 1u, le_mask = (2u << lane) - 1u;
-        const int slot = __popc(__ballot_sync(FULL, nrows > 0) & lt_mask);
-        int rtotal;
-        const int roff = warp_excl_scan(nrows, rtotal);
-        if (nrows > 0 && LT_IN_BOUNDS(slot < 32, &a.ctr->errors)) {
-          float4* R = reinterpret_cast<float4*>(recs + slot * kRec);
-          const bool flagged = may_need_exact(t, sig, delta);
-          const bool whole_rows = may_miss_fragments(t, sig, delta);
-          R[0] = make_float4(__int_as_float(qx0), __int_as_float(qy0), __int_as_float(qx1 | (whole_rows ? 0x10000 : 0)),
-                             __int_as_float(roff));
-          R[1] = make_float4(t.a[0], t.a[1], t.a[2], t.a[3]);
-          R[2] = make_float4(t.b[0], t.b[1], t.b[2], t.b[3]);
-          R[3] = make_float4(t.c[0], t.c[1], t.c[2], t.c[3]);
-          R[4] = make_float4(inv_or_zero(t.a[0]), inv_or_zero(t.a[1]), inv_or_zero(t.a[2]), inv_or_zero(t.a[3]));
-          const float flag = flagged ? 1.0f : 0.0f;
-          if (persp) {
-            R[5] = make_float4(t.pa[0], t.pb[0], t.pc[0], t.pa[1]);
-            R[6] = make_float4(t.pb[1], t.pc[1], t.g, flag);
+    for (long long cb = (long long)warp * kCB; cb < ncl; cb += (long long)nw * kCB) {
+      // ---- 0. lanes c and c + 16 project cube c: its anchor and corners 0-3 / 4-7
+      {
+        const int c = lane & (kCB - 1), hh = lane >> 4;
+        const long long cidx = cb + c;
+        bool ok = true, front = true;
+        unsigned zmask = 0;
+        float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f, w0 = 0.f;
+        if (cidx < ncl) {
+          const unsigned long long li = e0 + (unsigned long long)cidx;
+          const long long cube = LT_IN_BOUNDS(li < e1, &a.ctr->errors) ? (long long)a.list[li] : 0;
+          zmask = a.L.degen ? (unsigned)__ldg(a.L.degen + snap_off + cube) & 63u : 0u;
+          int i, j, k;
+          cube_ijk(a.L, cube, i, j, k);
+          float X0 = 0.f, Y0 = 0.f, Z0 = 1.f;
+          if (!persp) {
+            anchor_affine(F, 0, i, j, k, axh, axl);
+            anchor_affine(F, 1, i, j, k, ayh, ayl);
           } else {
-            R[6] = make_float4(0.f, 0.f, 0.f, flag);
+            float Xh, Xl, Yh, Yl, Zh, Zl;
+            anchor_affine(F, 0, i, j, k, Xh, Xl);
+            anchor_affine(F, 1, i, j, k, Yh, Yl);
+            anchor_affine(F, 2, i, j, k, Zh, Zl);
+            X0 = Xh + Xl; Y0 = Yh + Yl; Z0 = Zh + Zl;
+            front = Z0 > F.near_z;
+            const float rz = fast_rcp(Zh);
+            ff_project(Xh, Xl, Zh, Zl, rz, F.kxh, F.kxl, F.cx, axh, axl);
+            ff_project(Yh, Yl, Zh, Zl, rz, F.kyh, F.kyl, F.cy, ayh, ayl);
+            w0 = fast_rcp(Z0);
           }
-          R[7] = make_float4(t.st[0], t.st[1], t.st[2], t.st[3]);
-          R[8] = make_float4(__int_as_float(sx), __int_as_float(sy), __int_as_float(lane), delta);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int n = 4 * hh + q;
+            const float3 l = load_corner(a.L, snap_off, i, j, k, n, ok);
+            float4 cv;
+            if (!persp) {
+              cv.x = (F.r[0] * l.x + F.r[1] * l.y + F.r[2] * l.z) * F.sx;
+              cv.y = (F.u[0] * l.x + F.u[1] * l.y + F.u[2] * l.z) * F.sy;
+              cv.z = 0.f;
+              cv.w = 1.f;
+            } else {
+              const float dX = F.r[0] * l.x + F.r[1] * l.y + F.r[2] * l.z;
+              const float dY = F.u[0] * l.x + F.u[1] * l.y + F.u[2] * l.z;
+              const float dZ = F.f[0] * l.x + F.f[1] * l.y + F.f[2] * l.z;
+              const float Zn = Z0 + dZ;
+              front = front && (Zn > F.near_z);
+              const float inv = fast_rcp(Zn * Z0);
+              // X_n/Z_n - X0/Z0 = (dX Z0 - X0 dZ) / (Z_n Z0), free of cancellation
+              cv.x = (dX * Z0 - X0 * dZ) * inv * F.kx;
+              cv.y = (dY * Z0 - Y0 * dZ) * inv * F.ky;
+              cv.z = -dZ * inv;
+              cv.w = Zn;
+            }
+            S.cor[c * kCorStride + n] = cv;
+          }
         }
-        __syncwarp();
-        // The owner of a position in a 32-wide step is the last run starting
-        // at or before it: with runs compacted, its index is the number of
-        // runs started before the step plus those started in the step up to
-        // the position, minus one.
-        int rprev = 0;
-        for (int rb = 0; rb < rtotal; rb += 32) {
-          const int rrel = roff - rb;
-          const unsigned rmask = __reduce_or_sync(FULL, (nrows > 0 && rrel >= 0 && rrel < 32) ? (1u << rrel) : 0u);
-          const int o = rprev + __popc(rmask & le_mask) - 1;
-          rprev += __popc(rmask);
-          // ---- 3. pixel span of each job's row: every edge function >= 0
-          int len = 0, xa = 0, Yr = 0;
-          if (rb + lane < rtotal) {
-            const float4* R = reinterpret_cast<const float4*>(recs + o * kRec);
-            const float4 r0 = R[0];
-            Yr = __float_as_int(r0.y) + (rb + lane - __float_as_int(r0.w));
-            const float fy = (float)Yr;
-            const float4 ra = R[1], rbv = R[2], rc = R[3], ri = R[4];
-            float lo = __int_as_float(0xff800000), hi = __int_as_float(0x7f800000);
-            span_edge(ra.x, fmaf(rbv.x, fy, rc.x), ri.x, lo, hi);
-            span_edge(ra.y, fmaf(rbv.y, fy, rc.y), ri.y, lo, hi);
-            span_edge(ra.z, fmaf(rbv.z, fy, rc.z), ri.z, lo, hi);
-            span_edge(ra.w, fmaf(rbv.w, fy, rc.w), ri.w, lo, hi);
-            const int qx1w = __float_as_int(r0.z);
-            const float qx0f = (float)__float_as_int(r0.x), qx1f = (float)(qx1w & 0xffff);
-            if (qx1w >> 16) {
-              // a steep sliver: the whole bounding-box row, so that pixels the
-              // vertex uncertainty could move inside are checked too
-              lo = qx0f;
-              hi = qx1f;
-            }
-            lo = fmaxf(lo - 1e-3f, qx0f);
-            hi = fminf(hi + 1e-3f, qx1f);
-            if (lo <= hi) {
-              xa = (int)ceilf(lo);
-              len = max(0, (int)floorf(hi) - xa + 1);
+        // both halves of a cube must be finite and in front of the eye
+        const bool good = __shfl_xor_sync(FULL, (int)(ok && front), 16) && ok && front;
+        if (hh == 0) {
+          // perspective: the anchor's offset from the view axis times the
+          // depth offsets enters the vertex uncertainty (per corner |dw| / w0)
+          const float offw = persp ? __fdividef(fmaxf(fabsf(axh - F.cx), fabsf(ayh - F.cy)), w0) : 0.f;
+          const unsigned flags = zmask | ((cidx < ncl && good) ? kCubeValid : 0u);
+          S.anc[c] = make_float4(axh, axl, ayh, ayl);
+          S.cinfo[c] = make_float4(w0, offw, __int_as_float((int)flags), 0.f);
+        }
+      }
+      __syncwarp();
+#pragma unroll 1
+      for (int qr = 0; qr < kTB / 32; ++qr) {
+        // ---- 1. one tetrahedron per lane
+        const int ts = qr * 32 + lane;  // tetrahedron slot of the batch
+        const int c = ts / 6, s = ts - 6 * c;
+        const unsigned tau = (unsigned)((cb + c) * 6 + s);  // index within the tile's tetrahedra
+        const float4 ci = S.cinfo[c];
+        const unsigned cfl = (unsigned)__float_as_int(ci.z);
+        const bool ok = (cfl & kCubeValid) && !((cfl >> s) & 1u);  // zero volume: contributes nothing
+        float px[4], py[4], pdw[4], pz[4];
+        float4 an = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ok) {
+          an = S.anc[c];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float4 v = S.cor[c * kCorStride + tet_corner_dyn(s, k)];
+            px[k] = v.x; py[k] = v.y; pdw[k] = v.z; pz[k] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) { px[k] = 0.f; py[k] = 0.f; pdw[k] = 0.f; pz[k] = 1.f; }
+        }
+        float bx0 = 0.f, bx1 = -1.f, by0 = 0.f, by1 = -1.f;
+        int sx0 = 0, sx1 = -1, sy0 = 0, sy1 = -1;
+        if (ok) {
+          bx0 = fminf(fminf(px[0], px[1]), fminf(px[2], px[3]));
+          bx1 = fmaxf(fmaxf(px[0], px[1]), fmaxf(px[2], px[3]));
+          by0 = fminf(fminf(py[0], py[1]), fminf(py[2], py[3]));
+          by1 = fmaxf(fmaxf(py[0], py[1]), fmaxf(py[2], py[3]));
+          const float axa = an.x + an.y, aya = an.z + an.w;
+          shift_range(axa + bx0, axa + bx1, (float)tx0 - 0.5f, (float)(tx0 + tw) - 0.5f, (float)F.W, wrap, sx0, sx1);
+          shift_range(aya + by0, aya + by1, (float)ty0 - 0.5f, (float)(ty0 + th) - 0.5f, (float)F.H, wrap, sy0, sy1);
+          sx1 = min(sx1, sx0 + 63);
+          sy1 = min(sy1, sy0 + 63);
+        }
+        const int ncx = max(0, sx1 - sx0 + 1), ncp = ncx * max(0, sy1 - sy0 + 1);
+        float delta = 0.f;
+        if (ok) {
+          const float Rx = fmaxf(fmaxf(fabsf(px[0]), fabsf(px[1])), fmaxf(fabsf(px[2]), fabsf(px[3])));
+          const float Ry = fmaxf(fmaxf(fabsf(py[0]), fabsf(py[1])), fmaxf(fabsf(py[2]), fabsf(py[3])));
+          float Rv = fmaxf(Rx, Ry);
+          if (persp) Rv += ci.y * fmaxf(fmaxf(fabsf(pdw[0]), fabsf(pdw[1])), fmaxf(fabsf(pdw[2]), fabsf(pdw[3])));
+          delta = vertex_uncertainty(Rv, persp);
+        }
+        const float margin = 1e-3f + delta;
+        const int rounds = __reduce_max_sync(FULL, ncp);
+        float Kn = Kn0, invKn = 0.f;
+        if (persp && ok) {
+          Kn = __fdividef(Kn0, pz[0] * pz[1] * pz[2] * pz[3]);
+          invKn = fast_rcp(Kn);
+        }
+        for (int r = 0; r < rounds; ++r) {
+          int nrows = 0, qx0 = 0, qx1 = 0, qy0 = 0, sx = 0, sy = 0;
+          TetRaster t;
+          if (r < ncp) {
+            sx = sx0 + r % ncx;
+            sy = sy0 + r / ncx;
+            // vertex coordinates relative to the tile origin: anchor + shift - tile corner
+            const float ox = ((float)(tx0 - sx * F.W) - an.x) - an.y;
+            const float oy = ((float)(ty0 - sy * F.H) - an.z) - an.w;
+            const float x0 = px[0] - ox, x1 = px[1] - ox, x2 = px[2] - ox, x3 = px[3] - ox;
+            const float y0 = py[0] - oy, y1 = py[1] - oy, y2 = py[2] - oy, y3 = py[3] - oy;
+            qx0 = max(0, (int)ceilf(bx0 - ox - margin));
+            qx1 = min(tw - 1, (int)floorf(bx1 - ox + margin));
+            qy0 = max(0, (int)ceilf(by0 - oy - margin));
+            const int qy1 = min(th - 1, (int)floorf(by1 - oy + margin));
+            if (qx0 <= qx1 && qy0 <= qy1) {
+              const bool set =
+                  persp ? tet_setup<true>(x0, y0, x1, y1, x2, y2, x3, y3, pdw[0], pdw[1], pdw[2], pdw[3], Kn, ci.x,
+                                          invKn, t)
+                        : tet_setup<false>(x0, y0, x1, y1, x2, y2, x3, y3, 0.f, 0.f, 0.f, 0.f, Kn, 0.f, 0.f, t);
+              if (set) nrows = qy1 - qy0 + 1;
             }
           }
-          int ptotal;
-          const int poff = warp_excl_scan(len, ptotal);
-          const int jslot = __popc(__ballot_sync(FULL, len > 0) & lt_mask);
-          if (len > 0 && LT_IN_BOUNDS(jslot < 32 && o < 32, &a.ctr->errors)) jobs[jslot] = make_int4(xa, Yr, o, poff);
+          // ---- 2. records of the drawable tetrahedra, compacted, and the
+          // flattened (tetrahedron, row) jobs
+          const unsigned lt_mask = (1u << lane) - 1u, le_mask = (2u << lane) - 1u;
+          const int slot = __popc(__ballot_sync(FULL, nrows > 0) & lt_mask);
+          int rtotal;
+          const int roff = warp_excl_scan(nrows, rtotal);
+          if (nrows > 0 && LT_IN_BOUNDS(slot < 32, &a.ctr->errors)) {
+            float4* R = reinterpret_cast<float4*>(recs + slot * kRec);
+            const bool flagged = may_need_exact(t, sig, delta);
+            const bool whole_rows = may_miss_fragments(t, sig, delta);
+            R[0] = make_float4(__int_as_float(qx0), __int_as_float(qy0), __int_as_float(qx1 | (whole_rows ? 0x10000 : 0)),
+                               __int_as_float(roff));
+            R[1] = make_float4(t.a[0], t.a[1], t.a[2], t.a[3]);
+            R[2] = make_float4(t.b[0], t.b[1], t.b[2], t.b[3]);
+            R[3] = make_float4(t.c[0], t.c[1], t.c[2], t.c[3]);
+            R[4] = make_float4(inv_or_zero(t.a[0]), inv_or_zero(t.a[1]), inv_or_zero(t.a[2]), inv_or_zero(t.a[3]));
+            const float flag = flagged ? 1.0f : 0.0f;
+            if (persp) {
+              R[5] = make_float4(t.pa[0], t.pb[0], t.pc[0], t.pa[1]);
+              R[6] = make_float4(t.pb[1], t.pc[1], t.g, flag);
+            } else {
+              R[6] = make_float4(0.f, 0.f, 0.f, flag);
+            }
+            R[7] = make_float4(t.st[0], t.st[1], t.st[2], t.st[3]);
+            R[8] = make_float4(__int_as_float(sx), __int_as_float(sy), __int_as_float((int)tau), delta);
+          }
           __syncwarp();
-          // ---- 4. walk the pixels of the jobs, 32 per step
-          int pprev = 0;
-          for (int pb = 0; pb < ptotal; pb += 32) {
-            const int prel = poff - pb;
-            const unsigned pmask = __reduce_or_sync(FULL, (len > 0 && prel >= 0 && prel < 32) ? (1u << prel) : 0u);
-            const int j = pprev + __popc(pmask & le_mask) - 1;
-            pprev += __popc(pmask);
-            bool exact = false;
-            unsigned long long qent = 0;
-            float vq = 0.f;
-            int Xq = 0, Yq = 0;
-            if (pb + lane < ptotal) {
-              const int4 J = jobs[j];
-              const int X = J.x + (pb + lane - J.w), Y = J.y;
-              const float4* R = reinterpret_cast<const float4*>(recs + J.z * kRec);
-              const float fx = (float)X, fy = (float)Y;
-              const float4 ra = R[1], rbv = R[2], rc = R[3];
-              const float f0 = fmaf(ra.x, fx, fmaf(rbv.x, fy, rc.x));
-              const float f1 = fmaf(ra.y, fx, fmaf(rbv.y, fy, rc.y));
-              const float f2 = fmaf(ra.z, fx, fmaf(rbv.z, fy, rc.z));
-              const float f3 = fmaf(ra.w, fx, fmaf(rbv.w, fy, rc.w));
-              const float Tv = fmaxf(fminf(fminf(f0, f1), fminf(f2, f3)), 0.0f);
-              float v = Tv;
-              float4 r6 = make_float4(0.f, 0.f, 0.f, 0.f);
-              float M = 1.0f, den = 1.0f;
-              if (persp) {
-                const float4 r5 = R[5];
-                r6 = R[6];
-                M = fmaxf(fmaf(r5.x, fx, fmaf(r5.y, fy, r5.z)), fmaf(r5.w, fx, fmaf(r6.x, fy, r6.y)));
-                den = M * fmaf(r6.z, Tv, M);
-                v = __fdividef(Tv, den);
-              } else if (!COUNT) {
-                r6 = R[6];
+          // The owner of a position in a 32-wide step is the last run starting
+          // at or before it: with runs compacted, its index is the number of
+          // runs started before the step plus those started in the step up to
+          // the position, minus one.
+          int rprev = 0;
+          for (int rb = 0; rb < rtotal; rb += 32) {
+            const int rrel = roff - rb;
+            const unsigned rmask = __reduce_or_sync(FULL, (nrows > 0 && rrel >= 0 && rrel < 32) ? (1u << rrel) : 0u);
+            const int o = rprev + __popc(rmask & le_mask) - 1;
+            rprev += __popc(rmask);
+            // ---- 3. pixel span of each job's row: every edge function >= 0
+            int len = 0, xa = 0, Yr = 0;
+            if (rb + lane < rtotal) {
+              const float4* R = reinterpret_cast<const float4*>(recs + o * kRec);
+              const float4 r0 = R[0];
+              Yr = __float_as_int(r0.y) + (rb + lane - __float_as_int(r0.w));
+              const float fy = (float)Yr;
+              const float4 ra = R[1], rbv = R[2], rc = R[3], ri = R[4];
+              float lo = __int_as_float(0xff800000), hi = __int_as_float(0x7f800000);
+              span_edge(ra.x, fmaf(rbv.x, fy, rc.x), ri.x, lo, hi);
+              span_edge(ra.y, fmaf(rbv.y, fy, rc.y), ri.y, lo, hi);
+              span_edge(ra.z, fmaf(rbv.z, fy, rc.z), ri.z, lo, hi);
+              span_edge(ra.w, fmaf(rbv.w, fy, rc.w), ri.w, lo, hi);
+              const int qx1w = __float_as_int(r0.z);
+              const float qx0f = (float)__float_as_int(r0.x), qx1f = (float)(qx1w & 0xffff);
+              if (qx1w >> 16) {
+                // a steep sliver: the whole bounding-box row, so that pixels the
+                // vertex uncertainty could move inside are checked too
+                lo = qx0f;
+                hi = qx1f;
               }
-              if (COUNT) {
-                if (v > 0.0f) ++nfrag;
-              } else if (v > 0.0f || r6.w != 0.0f) {
-                // flagged tetrahedra: fragments whose error bound is too large,
-                // and pixels the vertex uncertainty could move inside, go to
-                // the exact evaluation
-                if (r6.w != 0.0f) {
-                  const float q = persp ? __fdividef(M, den) : 1.0f;  // d value / d T = (M / den)^2
-                  exact = fragment_needs_exact(f0, f1, f2, f3, ra, rbv, R[7], R[8].w, q * q, v, sig);
-                }
-                if (!exact) {
-                  if (v > 0.0f && LT_IN_BOUNDS(X >= 0 && X < tw && Y >= 0 && Y < th, &a.ctr->errors))
-                    accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], v, &a.ctr->errors);
-                } else {
-                  const float4 r8 = R[8];
-                  qent = pack_frag((unsigned)(tb + __float_as_int(r8.z)), __float_as_int(r8.x), __float_as_int(r8.y),
-                                   X, Y);
-                  vq = v;
-                  Xq = X;
-                  Yq = Y;
-                }
+              lo = fmaxf(lo - 1e-3f, qx0f);
+              hi = fminf(hi + 1e-3f, qx1f);
+              if (lo <= hi) {
+                xa = (int)ceilf(lo);
+                len = max(0, (int)floorf(hi) - xa + 1);
               }
             }
-            if (!COUNT) {
-              const unsigned em = __ballot_sync(FULL, exact);
-              if (em) {
-                const int leader = __ffs(em) - 1;
-                unsigned base = 0;
-                if (lane == leader) base = atomicAdd(&qn, (unsigned)__popc(em));
-                base = __shfl_sync(FULL, base, leader);
-                if (exact) {
-                  const unsigned slot = base + __popc(em & lt_mask);
-                  if (slot < a.xq_cap) {
-                    xq[slot] = qent;
-                  } else if (vq > 0.0f) {
-                    // queue full: keep the FP32 value (counted in the statistics)
-                    accum_fixed(&acc_lo[Yq * T + Xq], &acc_hi[Yq * T + Xq], vq, &a.ctr->errors);
+            int ptotal;
+            const int poff = warp_excl_scan(len, ptotal);
+            const int jslot = __popc(__ballot_sync(FULL, len > 0) & lt_mask);
+            if (len > 0 && LT_IN_BOUNDS(jslot < 32 && o < 32, &a.ctr->errors)) jobs[jslot] = make_int4(xa, Yr, o, poff);
+            __syncwarp();
+            // ---- 4. walk the pixels of the jobs, 32 per step
+            int pprev = 0;
+            for (int pb = 0; pb < ptotal; pb += 32) {
+              const int prel = poff - pb;
+              const unsigned pmask = __reduce_or_sync(FULL, (len > 0 && prel >= 0 && prel < 32) ? (1u << prel) : 0u);
+              const int j = pprev + __popc(pmask & le_mask) - 1;
+              pprev += __popc(pmask);
+              bool exact = false;
+              unsigned long long qent = 0;
+              float vq = 0.f;
+              int Xq = 0, Yq = 0;
+              if (pb + lane < ptotal) {
+                const int4 J = jobs[j];
+                const int X = J.x + (pb + lane - J.w), Y = J.y;
+                const float4* R = reinterpret_cast<const float4*>(recs + J.z * kRec);
+                const float fx = (float)X, fy = (float)Y;
+                const float4 ra = R[1], rbv = R[2], rc = R[3];
+                const float f0 = fmaf(ra.x, fx, fmaf(rbv.x, fy, rc.x));
+                const float f1 = fmaf(ra.y, fx, fmaf(rbv.y, fy, rc.y));
+                const float f2 = fmaf(ra.z, fx, fmaf(rbv.z, fy, rc.z));
+                const float f3 = fmaf(ra.w, fx, fmaf(rbv.w, fy, rc.w));
+                const float Tv = fmaxf(fminf(fminf(f0, f1), fminf(f2, f3)), 0.0f);
+                float v = Tv;
+                float4 r6 = make_float4(0.f, 0.f, 0.f, 0.f);
+                float M = 1.0f, den = 1.0f;
+                if (persp) {
+                  const float4 r5 = R[5];
+                  r6 = R[6];
+                  M = fmaxf(fmaf(r5.x, fx, fmaf(r5.y, fy, r5.z)), fmaf(r5.w, fx, fmaf(r6.x, fy, r6.y)));
+                  den = M * fmaf(r6.z, Tv, M);
+                  v = __fdividef(Tv, den);
+                } else if (!COUNT) {
+                  r6 = R[6];
+                }
+                if (COUNT) {
+                  if (v > 0.0f) ++nfrag;
+                } else if (v > 0.0f || r6.w != 0.0f) {
+                  // flagged tetrahedra: fragments whose error bound is too large,
+                  // and pixels the vertex uncertainty could move inside, go to
+                  // the exact evaluation
+                  if (r6.w != 0.0f) {
+                    const float q = persp ? __fdividef(M, den) : 1.0f;  // d value / d T = (M / den)^2
+                    exact = fragment_needs_exact(f0, f1, f2, f3, ra, rbv, R[7], R[8].w, q * q, v, sig);
+                  }
+                  if (!exact) {
+                    if (v > 0.0f && LT_IN_BOUNDS(X >= 0 && X < tw && Y >= 0 && Y < th, &a.ctr->errors))
+                      accum_fixed(&acc[Y * AS + X], v, a.ctr);
+                  } else {
+                    const float4 r8 = R[8];
+                    qent = pack_frag((unsigned)__float_as_int(r8.z), __float_as_int(r8.x), __float_as_int(r8.y),
+                                     X, Y);
+                    vq = v;
+                    Xq = X;
+                    Yq = Y;
                   }
                 }
               }
+              if (!COUNT) {
+                const unsigned em = __ballot_sync(FULL, exact);
+                if (em) {
+                  const int leader = __ffs(em) - 1;
+                  unsigned base = 0;
+                  if (lane == leader) base = atomicAdd(&qn, (unsigned)__popc(em));
+                  base = __shfl_sync(FULL, base, leader);
+                  if (exact) {
+                    const unsigned slot = base + __popc(em & lt_mask);
+                    if (slot < a.xq_cap) {
+                      xq[slot] = qent;
+                    } else if (vq > 0.0f) {
+                      // queue full: keep the FP32 value (counted in the statistics)
+                      accum_fixed(&acc[Yq * AS + Xq], vq, a.ctr);
+                    }
+                  }
+                }
+              }
+              __syncwarp();
             }
-            __syncwarp();
           }
         }
       }
-      cr += step_r;
-      cq += step_q + (cr >= 6u ? 1u : 0u);
-      cr = cr >= 6u ? cr - 6u : cr;
+      __syncwarp();
     }
     if (COUNT) {
       unsigned long long c = nfrag;
@@ -377,7 +464,7 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
       if (!LT_IN_BOUNDS(li < e1 && X < tw && Y < th, &a.ctr->errors)) continue;
       const long long cube = (long long)a.list[li];
       const double val = exact_fragment(a.L, F, cube, (int)(tau_o % 6), sxo, syo, tx0 + X, ty0 + Y, F.m_tet);
-      if (val > 0.0) accum_fixed(&acc_lo[Y * T + X], &acc_hi[Y * T + X], (float)(val / F.unit), &a.ctr->errors);
+      if (val > 0.0) accum_fixed(&acc[Y * AS + X], (float)(val / F.unit), a.ctr);
     }
     __syncthreads();
     // ---- one store per pixel, and the tile's share of the frame mass
@@ -385,9 +472,7 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
     float* img = a.image + (long long)f * a.image_stride;
     for (int li = threadIdx.x; li < tw * th; li += blockDim.x) {
       const int ly = li / tw, lx = li - ly * tw;
-      const int si = ly * T + lx;
-      const unsigned long long q = ((unsigned long long)acc_hi[si] << kAccLoBits) + (unsigned long long)acc_lo[si];
-      double v = (double)q * F.unit;
+      double v = (double)acc[ly * AS + lx] * F.unit;
       if (persp) {
         const float xt = F.tan_x * (2.0f * ((float)(tx0 + lx) + 0.5f) / (float)F.W - 1.0f);
         const float yt = F.tan_y * (2.0f * ((float)(ty0 + ly) + 0.5f) / (float)F.H - 1.0f);
@@ -413,7 +498,7 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
 
 static size_t tile_smem(int threads, int tile) {
   const int nw = threads / 32;
-  return sizeof(unsigned) * 2 * tile * tile + sizeof(float) * nw * 32 * kRec + sizeof(int4) * nw * 32;
+  return sizeof(WarpSmem) * nw + sizeof(unsigned long long) * tile * (tile + 5);
 }
 
 int raster_max_ctas_per_sm(int threads, int tile, int any_persp) {

@@ -313,3 +313,73 @@ def test_graph_replay_reports_bin_capacity_overflow():
     R.render_tiles()
     R.sync()
     assert R.get_stats()["entries"] > need_calm
+
+
+def test_accumulator_range_overflow_is_reported():
+    """Each pixel is summed in a 64-bit integer holding values below
+    2^(64 - frac_bits) mean column densities. With frac_bits = 62 (4 sigma)
+    the caustics of this frame (up to about 9 sigma) pass the range, and the
+    add that wraps a pixel's sum latches LT_ERR_RANGE; with frac_bits = 59
+    (32 sigma) the same frame fits and matches the oracle."""
+    from paper_1208_3206_gb300._lib import LtError
+    from paper_1208_3206_gb300.render import Renderer
+    N, W = 32, 256
+    pos = field(N, -2.0, 16.0, 1001).positions(4.0)
+    cam = ortho_z(W, W)
+    ref = oracle.render(pos, N, cam)
+    assert 4.0 < ref.max() < 32.0
+    R = Renderer(frac_bits=62)
+    R.build_tets(torch.from_numpy(pos).cuda(), N)
+    R.project_bin([cam])
+    R.render_tiles()
+    with pytest.raises(LtError) as e:
+        R.sync()
+    assert e.value.name == "LT_ERR_RANGE"
+    assert R.get_stats()["range_overflow"] > 0
+    R.set_config(frac_bits=59)
+    R.project_bin([cam])
+    img = R.render_tiles()
+    R.sync()
+    assert pixel_error(img[0].cpu().numpy(), ref, 1.0) <= PIX_TOL
+
+
+def test_graph_keeps_its_frames_and_goes_stale_when_buffers_move():
+    """A graph keeps its own copy of its views: a direct lt_project_bin with
+    other cameras between replays does not change what the graph renders. A
+    direct call that has to reallocate a buffer the graph captured (here:
+    ten times the tiles), and a new lt_build_tets, make the graph stale, and
+    lt_graph_launch refuses with LT_ERR_STATE until it is built again."""
+    from paper_1208_3206_gb300._lib import LtError
+    from paper_1208_3206_gb300.render import Renderer
+    R = Renderer(tile=16)
+    N = 16
+    f = field(N, -2.0, 6.0, 21)
+    pos = torch.from_numpy(np.concatenate([f.positions(1.0), f.positions(2.0)])).cuda()
+    cams = sphere_cameras(2, 64, 64)
+    R.build_tets(pos, N)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        img = R.graph_build(cams, [0, 1])
+        R.graph_launch()
+        R.sync()
+        first = img.clone()
+        # other views of the same size, binned directly: the graph's views stay
+        R.project_bin(sphere_cameras(5, 64, 64)[3:5], [1, 0])
+        R.render_tiles()
+        R.graph_launch()
+        R.sync()
+        assert torch.equal(img, first)
+        # many more tiles: the direct call reallocates the bins
+        R.project_bin([ortho_z(640, 640)] * 4)
+        with pytest.raises(LtError) as e:
+            R.graph_launch()
+        assert e.value.name == "LT_ERR_STATE"
+        R.graph_build(cams, [0, 1], image=img)
+        R.graph_launch()
+        R.sync()
+        assert torch.equal(img, first)
+        R.build_tets(pos, N)
+        with pytest.raises(LtError) as e:
+            R.graph_launch()
+        assert e.value.name == "LT_ERR_STATE"
+    torch.cuda.synchronize()
