@@ -16,4 +16,5 @@ from .oracle import (  # noqa: F401
     render_soup,
     resample,
     point_density,
+    centroids,
 )

@@ -13,6 +13,8 @@ the oracle pins its arithmetic:
     front-face sum, c the camera location; the pixel is back minus front.
   * `resample_barycentric`: the grid resampling of Sec. 4.3 with the same
     barycentric inside test along each cell column.
+  * `centroids_bruteforce`: the centroid splats of Sec. 4.2 over every
+    (pixel, tetrahedron, period) triple, in numpy.
 
 Both draw every periodic copy of every tetrahedron for periodic orthographic
 windows by brute force over image-period shifts in [-2, 2].
@@ -226,4 +228,31 @@ def resample_barycentric(pos, N: int, n: int, weight: str = "density", box: floa
                         seg = min(hi[p], (c + 1) * g) - max(lo[p], c * g)
                         if seg > 0:
                             out[c % n, b, a] += q * seg
+    return out
+
+
+def centroids_bruteforce(pos, N: int, W: int, H: int, lo=(0.0, 0.0), hi=(1.0, 1.0), box: float = 1.0,
+                         total_mass: float = 1.0) -> np.ndarray:
+    """Centroid splats for a periodic orthographic view along +z (right = +x,
+    up = +y) over the window [lo, hi]: every (pixel, tetrahedron, image-period
+    shift) triple, the 2D M4 cubic spline (unit integral) of smoothing length
+    |V|^(1/3) at the centroid, times the tetrahedron's mass."""
+    verts, _, vol = lattice_tets(pos, N, box, total_mass)
+    m = total_mass / (6.0 * N ** 3)
+    cen = verts.mean(axis=1)
+    lx, ly = hi[0] - lo[0], hi[1] - lo[1]
+    xs = lo[0] + (np.arange(W) + 0.5) * lx / W
+    ys = lo[1] + (np.arange(H) + 0.5) * ly / H
+    X, Y = np.meshgrid(xs, ys)  # [H][W]
+    out = np.zeros((H, W))
+    for t in range(len(vol)):
+        if vol[t] == 0.0:
+            continue
+        h = abs(vol[t]) ** (1.0 / 3.0)
+        norm = m * 10.0 / (7.0 * math.pi * h * h)
+        for sy in range(-2, 3):
+            for sx in range(-2, 3):
+                r = np.hypot(X - (cen[t, 0] - sx * lx), Y - (cen[t, 1] - sy * ly)) / h
+                w = np.where(r < 1.0, 1.0 - 1.5 * r ** 2 + 0.75 * r ** 3, np.where(r < 2.0, 0.25 * (2.0 - r) ** 3, 0.0))
+                out += norm * w
     return out

@@ -665,3 +665,85 @@ int orc_point_density(const double* pos, int N, double box, double total_mass, c
   free(bufs);
   return ORC_OK;
 }
+
+/*
+ * Centroid splats (Sec. 4.2): every tetrahedron T drawn as a 2D kernel in
+ * the image plane, centred on the projection of its centroid
+ * c_T = (v0 + v1 + v2 + v3) / 4 (its centre of mass, the density being
+ * constant), scaled with (m / rho_T)^(1/3) = |V_T|^(1/3) and carrying its
+ * mass m. The paper names a cubic-spline kernel and leaves its form and the
+ * scale factor open; this oracle takes the 2D M4 cubic spline with unit
+ * integral and smoothing length h_T = |V_T|^(1/3):
+ *   W(r, h) = 10 / (7 pi h^2) * w(r / h),
+ *   w(q) = 1 - 3/2 q^2 + 3/4 q^3 (q < 1), (2 - q)^3 / 4 (1 <= q < 2), 0 else.
+ * A pixel holds the sum over tetrahedra of m W(distance in the image plane
+ * between its centre and the projected centroid, h_T): an estimate of the
+ * column density. Orthographic views only (the billboards face the view
+ * direction, so their projection keeps its size); a periodic window (wrap)
+ * draws every periodic copy, like orc_render. Tetrahedra with V == 0 carry
+ * no splat (their scale is zero). out: [H][W].
+ */
+static double spline_w(double q) {
+  if (q < 1.0) return 1.0 - 1.5 * q * q + 0.75 * q * q * q;
+  if (q < 2.0) { const double t = 2.0 - q; return 0.25 * t * t * t; }
+  return 0.0;
+}
+
+int orc_centroids(const double* pos, int N, double box, double total_mass, const orc_camera* cam, double* out,
+                  int nthreads) {
+  frame_t fr;
+  if (N <= 0 || box <= 0 || frame_init(cam, &fr) != ORC_OK || fr.persp) return ORC_ERR_ARG;
+  const long npix = (long)fr.W * fr.H;
+  const int T = num_threads(nthreads);
+  double* bufs = (double*)calloc((size_t)T * npix, sizeof(double));
+  const double m = total_mass / (6.0 * (double)N * N * N);
+  const double dx = (fr.hi[0] - fr.lo[0]) / fr.W, dy = (fr.hi[1] - fr.lo[1]) / fr.H;
+  const long ncubes = (long)N * N * N;
+#pragma omp parallel num_threads(T)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double* img = bufs + (size_t)tid * npix;
+#pragma omp for schedule(static)
+    for (long cube = 0; cube < ncubes; ++cube) {
+      long i = cube % N, j = (cube / N) % N, k = cube / ((long)N * N);
+      for (int s = 0; s < 6; ++s) {
+        double v[4][3];
+        tet_vertices(pos, N, box, i, j, k, s, v);
+        const double V = tet_volume(v);
+        if (V == 0.0) continue;
+        double c[3];
+        for (int q = 0; q < 3; ++q) c[q] = 0.25 * (v[0][q] + v[1][q] + v[2][q] + v[3][q]);
+        const double h = cbrt(fabs(V));
+        const double norm = m * 10.0 / (7.0 * M_PI * h * h);
+        const double a = dot3(fr.r, c), b = dot3(fr.u, c);  /* centroid in window coordinates */
+        /* pixels whose centre lies within 2h of the centroid (unwrapped indices) */
+        const long x0 = (long)ceil((a - 2.0 * h - fr.lo[0]) / dx - 0.5), x1 = (long)floor((a + 2.0 * h - fr.lo[0]) / dx - 0.5);
+        const long y0 = (long)ceil((b - 2.0 * h - fr.lo[1]) / dy - 0.5), y1 = (long)floor((b + 2.0 * h - fr.lo[1]) / dy - 0.5);
+        if (x0 > x1 || y0 > y1) continue;
+        long sx0, sx1, sy0, sy1;
+        shift_range(x0, x1, 0, fr.W - 1, fr.W, fr.wrap, &sx0, &sx1);
+        shift_range(y0, y1, 0, fr.H - 1, fr.H, fr.wrap, &sy0, &sy1);
+        for (long sy = sy0; sy <= sy1; ++sy)
+          for (long sx = sx0; sx <= sx1; ++sx) {
+            const long px0 = x0 > -sx * fr.W ? x0 : -sx * fr.W, px1 = x1 < fr.W - 1 - sx * fr.W ? x1 : fr.W - 1 - sx * fr.W;
+            const long py0 = y0 > -sy * fr.H ? y0 : -sy * fr.H, py1 = y1 < fr.H - 1 - sy * fr.H ? y1 : fr.H - 1 - sy * fr.H;
+            for (long py = py0; py <= py1; ++py)
+              for (long px = px0; px <= px1; ++px) {
+                const double xw = fr.lo[0] + (px + 0.5) * dx, yw = fr.lo[1] + (py + 0.5) * dy;
+                const double r = sqrt((xw - a) * (xw - a) + (yw - b) * (yw - b));
+                const double w = spline_w(r / h);
+                if (w > 0.0) img[(py + sy * fr.H) * fr.W + (px + sx * fr.W)] += norm * w;
+              }
+          }
+      }
+    }
+  }
+  memset(out, 0, sizeof(double) * npix);
+  for (int t = 0; t < T; ++t)
+    for (long p = 0; p < npix; ++p) out[p] += bufs[(size_t)t * npix + p];
+  free(bufs);
+  return ORC_OK;
+}

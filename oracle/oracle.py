@@ -95,6 +95,8 @@ def _load():
         lib.orc_resample.restype = C.c_int
         lib.orc_point_density.argtypes = [dp, C.c_int, C.c_double, C.c_double, dp, C.c_long, C.c_int, dp, C.c_int]
         lib.orc_point_density.restype = C.c_int
+        lib.orc_centroids.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.POINTER(_Cam), dp, C.c_int]
+        lib.orc_centroids.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -249,3 +251,19 @@ def point_density(pos, N: int, points, weight: str = "density", box: float = 1.0
     if rc != 0:
         raise RuntimeError(f"oracle point_density failed with code {rc}")
     return out[:pts.shape[0]]
+
+
+def centroids(pos, N: int, cam, box: float = 1.0, total_mass: float = 1.0, nthreads: int = 0) -> np.ndarray:
+    """Centroid splats (Sec. 4.2) of every tetrahedron in an orthographic
+    view: the 2D M4 cubic spline of unit integral with smoothing length
+    |V|^(1/3) at the projected centroid, weighted by the tetrahedron's mass.
+    Returns [H][W] float64."""
+    lib = _load()
+    cam = _cam(cam)
+    p = _pos64(pos, N)
+    out = np.zeros((cam.H, cam.W), dtype=np.float64)
+    cc = cam.to_c()
+    rc = lib.orc_centroids(_ptr(p, C.c_double), N, box, total_mass, C.byref(cc), _ptr(out, C.c_double), nthreads)
+    if rc != 0:
+        raise RuntimeError(f"oracle centroids failed with code {rc}")
+    return out

@@ -537,3 +537,58 @@ def test_render_crops_equal_slices_of_the_full_frame(view):
     single, nf_one, _ = oracle.render_crops(pos, N, cam, [(0, 0, cam["W"], cam["H"])])
     np.testing.assert_array_equal(single[0], full)
     assert nf_one == nf_full
+
+
+def test_centroid_kernel_has_unit_integral():
+    """The 2D M4 cubic spline of the centroid splats integrates to 1 over the
+    plane: one tetrahedron's splat carries its mass (midpoint rule on a fine
+    polar grid, independent of the oracle)."""
+    h = 0.37
+    r = (np.arange(20000) + 0.5) * (2.0 * h / 20000)
+    q = r / h
+    w = np.where(q < 1.0, 1.0 - 1.5 * q ** 2 + 0.75 * q ** 3, 0.25 * (2.0 - q) ** 3)
+    integral = float(np.sum(10.0 / (7.0 * math.pi * h * h) * w * 2.0 * math.pi * r) * (2.0 * h / 20000))
+    assert abs(integral - 1.0) <= 1e-8
+
+
+@pytest.mark.parametrize("N,W,lam,seed", [(1, 24, 0.0, 0), (2, 20, 0.6, 3), (3, 17, 1.1, 8)])
+def test_centroids_match_bruteforce(N, W, lam, seed):
+    """The oracle's splats against an independent numpy evaluation of every
+    (pixel, tetrahedron, period) triple on tiny lattices, including the
+    undeformed unit cube (N = 1) and a ragged window."""
+    rng = np.random.default_rng(seed)
+    # tiny lattices have no Zel'dovich modes below Nyquist: seeded random
+    # displacements of up to lam / 3 of a cell instead
+    pos = lattice_positions(N) if lam == 0.0 else lattice_positions(
+        N, disp=lambda q: rng.uniform(-lam / 3, lam / 3, q.shape) / N)
+    cam = ortho_z(W, W + 3)
+    ref = bf.centroids_bruteforce(pos, N, W, W + 3)
+    got = oracle.centroids(pos, N, cam)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_centroid_frame_mass_converges_to_total_mass():
+    """Over the periodic box window the splats carry the whole mass: the
+    pixel-centre sum times the pixel area tends to 1 as the pixels shrink
+    relative to the splats."""
+    N = 4
+    pos = ZeldovichField.generate(N, -2.0, 2.0, 11).positions(0.8)
+    errs = []
+    for W in (16, 32, 64):
+        img = oracle.centroids(pos, N, ortho_z(W, W))
+        errs.append(abs(img.sum() / (W * W) - 1.0))
+    assert errs[2] <= 1e-4
+    assert errs[2] < errs[0]
+
+
+def test_centroids_shift_with_the_particles():
+    """Moving every particle by exactly one pixel along x moves the periodic
+    image by one pixel."""
+    N, W = 4, 32
+    pos = ZeldovichField.generate(N, -2.0, 2.0, 12).positions(0.9).astype(np.float64)
+    cam = ortho_z(W, W)
+    a = oracle.centroids(pos, N, cam)
+    moved = pos.copy()
+    moved[:, 0] = np.mod(moved[:, 0] + 1.0 / W, 1.0)
+    b = oracle.centroids(moved, N, cam)
+    np.testing.assert_allclose(np.roll(a, 1, axis=1), b, rtol=1e-9, atol=1e-9)
