@@ -17,4 +17,5 @@ from .oracle import (  # noqa: F401
     resample,
     point_density,
     centroids,
+    hybrid,
 )

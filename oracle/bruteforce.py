@@ -256,3 +256,40 @@ def centroids_bruteforce(pos, N: int, W: int, H: int, lo=(0.0, 0.0), hi=(1.0, 1.
                 w = np.where(r < 1.0, 1.0 - 1.5 * r ** 2 + 0.75 * r ** 3, np.where(r < 2.0, 0.25 * (2.0 - r) ** 3, 0.0))
                 out += norm * w
     return out
+
+
+def splats_perspective_bruteforce(verts, W: int, H: int, eye, fwd, up, fov_y_deg: float, total_mass: float,
+                                  N: int) -> np.ndarray:
+    """Perspective centroid splats of the given tetrahedra [n][4][3]: for every
+    (pixel, tetrahedron), the ray through the pixel centre meets the
+    billboard (through the centroid, normal to the view direction) at a point
+    d from the centroid; the pixel adds m W(d, |V|^(1/3)) over the cosine of
+    the ray's angle to the view direction."""
+    f = np.asarray(fwd, dtype=np.float64)
+    f = f / np.linalg.norm(f)
+    r = np.cross(np.asarray(up, dtype=np.float64), f)
+    r = r / np.linalg.norm(r)
+    u = np.cross(f, r)
+    ty = math.tan(math.radians(fov_y_deg) / 2.0)
+    tx = ty * W / H
+    xt = tx * (2.0 * (np.arange(W) + 0.5) / W - 1.0)
+    yt = ty * (2.0 * (np.arange(H) + 0.5) / H - 1.0)
+    XT, YT = np.meshgrid(xt, yt)
+    e0 = np.asarray(eye, dtype=np.float64)
+    m = total_mass / (6.0 * N ** 3)
+    out = np.zeros((H, W))
+    for v in verts:
+        vol = np.dot(v[1] - v[0], np.cross(v[2] - v[0], v[3] - v[0])) / 6.0
+        if vol == 0.0:
+            continue
+        c = v.mean(axis=0) - e0
+        Z, X, Y = c @ f, c @ r, c @ u
+        if Z <= 0.0:
+            continue
+        # the ray e0 + t (f + xt r + yt u) meets the plane through the centroid at t = Z
+        d = np.hypot(Z * XT - X, Z * YT - Y)
+        h = abs(vol) ** (1.0 / 3.0)
+        q = d / h
+        w = np.where(q < 1.0, 1.0 - 1.5 * q ** 2 + 0.75 * q ** 3, np.where(q < 2.0, 0.25 * (2.0 - q) ** 3, 0.0))
+        out += m * 10.0 / (7.0 * math.pi * h * h) * w * np.sqrt(1.0 + XT ** 2 + YT ** 2)
+    return out

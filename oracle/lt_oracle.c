@@ -667,21 +667,31 @@ int orc_point_density(const double* pos, int N, double box, double total_mass, c
 }
 
 /*
- * Centroid splats (Sec. 4.2): every tetrahedron T drawn as a 2D kernel in
- * the image plane, centred on the projection of its centroid
- * c_T = (v0 + v1 + v2 + v3) / 4 (its centre of mass, the density being
- * constant), scaled with (m / rho_T)^(1/3) = |V_T|^(1/3) and carrying its
- * mass m. The paper names a cubic-spline kernel and leaves its form and the
- * scale factor open; this oracle takes the 2D M4 cubic spline with unit
- * integral and smoothing length h_T = |V_T|^(1/3):
+ * Centroid splats (Sec. 4.2): every tetrahedron T drawn as a 2D kernel on a
+ * billboard through its centroid c_T = (v0 + v1 + v2 + v3) / 4 (its centre of
+ * mass, the density being constant), facing the view direction, scaled with
+ * (m / rho_T)^(1/3) = |V_T|^(1/3) and carrying its mass m. The paper names a
+ * cubic-spline kernel and leaves its form and the scale factor open; this
+ * oracle takes the 2D M4 cubic spline with unit integral and smoothing
+ * length h_T = |V_T|^(1/3):
  *   W(r, h) = 10 / (7 pi h^2) * w(r / h),
  *   w(q) = 1 - 3/2 q^2 + 3/4 q^3 (q < 1), (2 - q)^3 / 4 (1 <= q < 2), 0 else.
- * A pixel holds the sum over tetrahedra of m W(distance in the image plane
- * between its centre and the projected centroid, h_T): an estimate of the
- * column density. Orthographic views only (the billboards face the view
- * direction, so their projection keeps its size); a periodic window (wrap)
- * draws every periodic copy, like orc_render. Tetrahedra with V == 0 carry
- * no splat (their scale is zero). out: [H][W].
+ * The billboard holds surface density m W(d, h), d the distance from c_T to
+ * the point where the pixel's ray crosses the billboard's plane, so the ray
+ * picks up m W(d, h) / cos(theta), theta its angle to the view direction:
+ *   orthographic: cos = 1 and d is the distance in the image plane;
+ *   perspective: with camera coordinates (X, Y, Z) of c_T and the pixel's
+ *     ray direction (xt, yt, 1), d = |(Z xt - X, Z yt - Y)| and
+ *     1 / cos = |(xt, yt, 1)|. Billboards with Z <= 0 are not drawn.
+ * A pixel holds the sum over tetrahedra (an estimate of the column density).
+ * A periodic orthographic window draws every periodic copy, like
+ * orc_render. Tetrahedra with V == 0 carry no splat.
+ *
+ * Hybrid near/far rendering (Sec. 6, Fig. "LargeScale"): with r_near > 0
+ * (perspective views only), the cubes whose corner-0 particle lies within
+ * r_near of the eye are drawn by the exact projection of Eq. 6 (the chords
+ * of orc_render) and only the other cubes' tetrahedra as splats. r_near = 0
+ * gives splats only. out: [H][W].
  */
 static double spline_w(double q) {
   if (q < 1.0) return 1.0 - 1.5 * q * q + 0.75 * q * q * q;
@@ -689,15 +699,18 @@ static double spline_w(double q) {
   return 0.0;
 }
 
-int orc_centroids(const double* pos, int N, double box, double total_mass, const orc_camera* cam, double* out,
-                  int nthreads) {
+int orc_hybrid(const double* pos, int N, double box, double total_mass, const orc_camera* cam, double r_near,
+               double* out, int nthreads) {
   frame_t fr;
-  if (N <= 0 || box <= 0 || frame_init(cam, &fr) != ORC_OK || fr.persp) return ORC_ERR_ARG;
+  if (N <= 0 || box <= 0 || !(r_near >= 0.0) || frame_init(cam, &fr) != ORC_OK) return ORC_ERR_ARG;
+  if (r_near > 0.0 && !fr.persp) return ORC_ERR_ARG;
   const long npix = (long)fr.W * fr.H;
   const int T = num_threads(nthreads);
   double* bufs = (double*)calloc((size_t)T * npix, sizeof(double));
+  int* errs = (int*)calloc(T, sizeof(int));
   const double m = total_mass / (6.0 * (double)N * N * N);
   const double dx = (fr.hi[0] - fr.lo[0]) / fr.W, dy = (fr.hi[1] - fr.lo[1]) / fr.H;
+  const double ptx = 2.0 * fr.tan_x / fr.W, pty = 2.0 * fr.tan_y / fr.H;  /* perspective pixel size in tan units */
   const long ncubes = (long)N * N * N;
 #pragma omp parallel num_threads(T)
   {
@@ -709,41 +722,100 @@ int orc_centroids(const double* pos, int N, double box, double total_mass, const
 #pragma omp for schedule(static)
     for (long cube = 0; cube < ncubes; ++cube) {
       long i = cube % N, j = (cube / N) % N, k = cube / ((long)N * N);
+      int near = 0;
+      if (r_near > 0.0) {
+        double c0[3], e[3];
+        corner_position(pos, N, box, i, j, k, c0);
+        sub3(c0, fr.eye, e);
+        near = dot3(e, e) < r_near * r_near;
+      }
       for (int s = 0; s < 6; ++s) {
         double v[4][3];
         tet_vertices(pos, N, box, i, j, k, s, v);
         const double V = tet_volume(v);
         if (V == 0.0) continue;
+        if (near) {
+          /* exact projection (Eq. 6), as in orc_render */
+          const double rho = m / fabs(V);
+          long bx0, bx1, by0, by1;
+          if (tet_pixel_box(&fr, v, &bx0, &bx1, &by0, &by1) < 0) { errs[tid] = ORC_ERR_BEHIND_EYE; continue; }
+          if (bx0 < 0) bx0 = 0;
+          if (by0 < 0) by0 = 0;
+          if (bx1 > fr.W - 1) bx1 = fr.W - 1;
+          if (by1 > fr.H - 1) by1 = fr.H - 1;
+          for (long py = by0; py <= by1; ++py)
+            for (long px = bx0; px <= bx1; ++px) {
+              double o[3], d[3];
+              pixel_ray(&fr, px, py, o, d);
+              const double dl = ray_chord(v, o, d, fr.persp, NULL, NULL, NULL, NULL);
+              if (dl > 0.0) img[py * fr.W + px] += rho * dl;
+            }
+          continue;
+        }
         double c[3];
         for (int q = 0; q < 3; ++q) c[q] = 0.25 * (v[0][q] + v[1][q] + v[2][q] + v[3][q]);
         const double h = cbrt(fabs(V));
         const double norm = m * 10.0 / (7.0 * M_PI * h * h);
-        const double a = dot3(fr.r, c), b = dot3(fr.u, c);  /* centroid in window coordinates */
-        /* pixels whose centre lies within 2h of the centroid (unwrapped indices) */
-        const long x0 = (long)ceil((a - 2.0 * h - fr.lo[0]) / dx - 0.5), x1 = (long)floor((a + 2.0 * h - fr.lo[0]) / dx - 0.5);
-        const long y0 = (long)ceil((b - 2.0 * h - fr.lo[1]) / dy - 0.5), y1 = (long)floor((b + 2.0 * h - fr.lo[1]) / dy - 0.5);
-        if (x0 > x1 || y0 > y1) continue;
-        long sx0, sx1, sy0, sy1;
-        shift_range(x0, x1, 0, fr.W - 1, fr.W, fr.wrap, &sx0, &sx1);
-        shift_range(y0, y1, 0, fr.H - 1, fr.H, fr.wrap, &sy0, &sy1);
-        for (long sy = sy0; sy <= sy1; ++sy)
-          for (long sx = sx0; sx <= sx1; ++sx) {
-            const long px0 = x0 > -sx * fr.W ? x0 : -sx * fr.W, px1 = x1 < fr.W - 1 - sx * fr.W ? x1 : fr.W - 1 - sx * fr.W;
-            const long py0 = y0 > -sy * fr.H ? y0 : -sy * fr.H, py1 = y1 < fr.H - 1 - sy * fr.H ? y1 : fr.H - 1 - sy * fr.H;
-            for (long py = py0; py <= py1; ++py)
-              for (long px = px0; px <= px1; ++px) {
-                const double xw = fr.lo[0] + (px + 0.5) * dx, yw = fr.lo[1] + (py + 0.5) * dy;
-                const double r = sqrt((xw - a) * (xw - a) + (yw - b) * (yw - b));
-                const double w = spline_w(r / h);
-                if (w > 0.0) img[(py + sy * fr.H) * fr.W + (px + sx * fr.W)] += norm * w;
-              }
-          }
+        if (!fr.persp) {
+          const double a = dot3(fr.r, c), b = dot3(fr.u, c);  /* centroid in window coordinates */
+          /* pixels whose centre lies within 2h of the centroid (unwrapped indices) */
+          const long x0 = (long)ceil((a - 2.0 * h - fr.lo[0]) / dx - 0.5), x1 = (long)floor((a + 2.0 * h - fr.lo[0]) / dx - 0.5);
+          const long y0 = (long)ceil((b - 2.0 * h - fr.lo[1]) / dy - 0.5), y1 = (long)floor((b + 2.0 * h - fr.lo[1]) / dy - 0.5);
+          if (x0 > x1 || y0 > y1) continue;
+          long sx0, sx1, sy0, sy1;
+          shift_range(x0, x1, 0, fr.W - 1, fr.W, fr.wrap, &sx0, &sx1);
+          shift_range(y0, y1, 0, fr.H - 1, fr.H, fr.wrap, &sy0, &sy1);
+          for (long sy = sy0; sy <= sy1; ++sy)
+            for (long sx = sx0; sx <= sx1; ++sx) {
+              const long px0 = x0 > -sx * fr.W ? x0 : -sx * fr.W, px1 = x1 < fr.W - 1 - sx * fr.W ? x1 : fr.W - 1 - sx * fr.W;
+              const long py0 = y0 > -sy * fr.H ? y0 : -sy * fr.H, py1 = y1 < fr.H - 1 - sy * fr.H ? y1 : fr.H - 1 - sy * fr.H;
+              for (long py = py0; py <= py1; ++py)
+                for (long px = px0; px <= px1; ++px) {
+                  const double xw = fr.lo[0] + (px + 0.5) * dx, yw = fr.lo[1] + (py + 0.5) * dy;
+                  const double r = sqrt((xw - a) * (xw - a) + (yw - b) * (yw - b));
+                  const double w = spline_w(r / h);
+                  if (w > 0.0) img[(py + sy * fr.H) * fr.W + (px + sx * fr.W)] += norm * w;
+                }
+            }
+        } else {
+          double e[3];
+          sub3(c, fr.eye, e);
+          const double Z = dot3(fr.f, e), X = dot3(fr.r, e), Y = dot3(fr.u, e);
+          if (!(Z > 0.0)) continue;
+          /* pixel centre xt = tan_x (2 (px + 1/2) / W - 1): the ray meets the billboard
+           * at distance Z |xt - X/Z| along r; the support is |d| < 2h */
+          const double cx = (X / Z / fr.tan_x + 1.0) * 0.5 * fr.W - 0.5, cy = (Y / Z / fr.tan_y + 1.0) * 0.5 * fr.H - 0.5;
+          const double rx = 2.0 * h / Z / ptx, ry = 2.0 * h / Z / pty;
+          long x0 = (long)ceil(cx - rx), x1 = (long)floor(cx + rx), y0 = (long)ceil(cy - ry), y1 = (long)floor(cy + ry);
+          if (x0 < 0) x0 = 0;
+          if (y0 < 0) y0 = 0;
+          if (x1 > fr.W - 1) x1 = fr.W - 1;
+          if (y1 > fr.H - 1) y1 = fr.H - 1;
+          for (long py = y0; py <= y1; ++py)
+            for (long px = x0; px <= x1; ++px) {
+              const double xt = fr.tan_x * (2.0 * (px + 0.5) / fr.W - 1.0);
+              const double yt = fr.tan_y * (2.0 * (py + 0.5) / fr.H - 1.0);
+              const double ddx = Z * xt - X, ddy = Z * yt - Y;
+              const double w = spline_w(sqrt(ddx * ddx + ddy * ddy) / h);
+              if (w > 0.0) img[py * fr.W + px] += norm * w * sqrt(1.0 + xt * xt + yt * yt);
+            }
+        }
       }
     }
   }
   memset(out, 0, sizeof(double) * npix);
-  for (int t = 0; t < T; ++t)
+  int err = ORC_OK;
+  for (int t = 0; t < T; ++t) {
     for (long p = 0; p < npix; ++p) out[p] += bufs[(size_t)t * npix + p];
+    if (errs[t]) err = errs[t];
+  }
   free(bufs);
-  return ORC_OK;
+  free(errs);
+  return err;
+}
+
+/* Centroid splats of every tetrahedron: orc_hybrid with r_near = 0. */
+int orc_centroids(const double* pos, int N, double box, double total_mass, const orc_camera* cam, double* out,
+                  int nthreads) {
+  return orc_hybrid(pos, N, box, total_mass, cam, 0.0, out, nthreads);
 }

@@ -97,6 +97,8 @@ def _load():
         lib.orc_point_density.restype = C.c_int
         lib.orc_centroids.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.POINTER(_Cam), dp, C.c_int]
         lib.orc_centroids.restype = C.c_int
+        lib.orc_hybrid.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.POINTER(_Cam), C.c_double, dp, C.c_int]
+        lib.orc_hybrid.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -254,10 +256,11 @@ def point_density(pos, N: int, points, weight: str = "density", box: float = 1.0
 
 
 def centroids(pos, N: int, cam, box: float = 1.0, total_mass: float = 1.0, nthreads: int = 0) -> np.ndarray:
-    """Centroid splats (Sec. 4.2) of every tetrahedron in an orthographic
-    view: the 2D M4 cubic spline of unit integral with smoothing length
-    |V|^(1/3) at the projected centroid, weighted by the tetrahedron's mass.
-    Returns [H][W] float64."""
+    """Centroid splats (Sec. 4.2) of every tetrahedron: the 2D M4 cubic
+    spline of unit integral with smoothing length |V|^(1/3) on a billboard
+    through the centroid facing the view, weighted by the tetrahedron's
+    mass (perspective rays pick it up over the cosine of their angle to the
+    view direction). Returns [H][W] float64."""
     lib = _load()
     cam = _cam(cam)
     p = _pos64(pos, N)
@@ -266,4 +269,21 @@ def centroids(pos, N: int, cam, box: float = 1.0, total_mass: float = 1.0, nthre
     rc = lib.orc_centroids(_ptr(p, C.c_double), N, box, total_mass, C.byref(cc), _ptr(out, C.c_double), nthreads)
     if rc != 0:
         raise RuntimeError(f"oracle centroids failed with code {rc}")
+    return out
+
+
+def hybrid(pos, N: int, cam, r_near: float, box: float = 1.0, total_mass: float = 1.0,
+           nthreads: int = 0) -> np.ndarray:
+    """Hybrid near/far rendering of a perspective view: cubes whose corner-0
+    particle lies within r_near of the eye by the exact projection (Eq. 6),
+    the others' tetrahedra as centroid splats. Returns [H][W] float64."""
+    lib = _load()
+    cam = _cam(cam)
+    p = _pos64(pos, N)
+    out = np.zeros((cam.H, cam.W), dtype=np.float64)
+    cc = cam.to_c()
+    rc = lib.orc_hybrid(_ptr(p, C.c_double), N, box, total_mass, C.byref(cc), float(r_near), _ptr(out, C.c_double),
+                        nthreads)
+    if rc != 0:
+        raise RuntimeError(f"oracle hybrid failed with code {rc}")
     return out

@@ -592,3 +592,55 @@ def test_centroids_shift_with_the_particles():
     moved[:, 0] = np.mod(moved[:, 0] + 1.0 / W, 1.0)
     b = oracle.centroids(moved, N, cam)
     np.testing.assert_allclose(np.roll(a, 1, axis=1), b, rtol=1e-9, atol=1e-9)
+
+
+def test_perspective_centroids_match_bruteforce():
+    """Perspective splats against an independent numpy evaluation over every
+    (pixel, tetrahedron) pair."""
+    N = 3
+    rng = np.random.default_rng(21)
+    pos = lattice_positions(N, disp=lambda q: rng.uniform(-0.3, 0.3, q.shape) / N)
+    cam = camera_dict("persp", 40, 34, eye=(0.4, -1.1, 0.7), fwd=(0.1, 1.5, -0.3), up=(0, 0, 1), fov_y_deg=50)
+    verts, _, _ = bf.lattice_tets(pos, N)
+    ref = bf.splats_perspective_bruteforce(verts, 40, 34, cam["eye"], cam["fwd"], cam["up"], 50.0, 1.0, N)
+    got = oracle.centroids(pos, N, cam)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_hybrid_limits_and_split():
+    """Hybrid near/far rendering: r_near beyond every cube is the exact
+    projection, r_near = 0 the splats; in between, the near cubes' exact
+    chords (through the tetrahedron-soup projection) plus the far cubes'
+    splats (numpy), with near decided by the cube's corner-0 particle."""
+    N = 4
+    rng = np.random.default_rng(22)
+    pos = lattice_positions(N, disp=lambda q: rng.uniform(-0.3, 0.3, q.shape) / N)
+    cam = camera_dict("persp", 36, 30, eye=(0.5, -0.9, 0.55), fwd=(0.0, 1.0, 0.0), up=(0, 0, 1), fov_y_deg=55)
+    np.testing.assert_array_equal(oracle.hybrid(pos, N, cam, 1e30), oracle.render(pos, N, cam))
+    np.testing.assert_array_equal(oracle.hybrid(pos, N, cam, 0.0), oracle.centroids(pos, N, cam))
+    r_near = 1.4
+    verts, rho, _ = bf.lattice_tets(pos, N)
+    p = np.asarray(pos, dtype=np.float64)[:, :3]
+    idx = np.arange(N ** 3)
+    q = np.stack([idx % N, (idx // N) % N, idx // (N * N)], axis=1) / N
+    d = p - q
+    d -= np.round(d)
+    near_cube = np.linalg.norm(q + d - np.asarray(cam["eye"]), axis=1) < r_near
+    near = np.repeat(near_cube, 6)
+    assert 0 < near.sum() < near.size
+    ref = oracle.render_soup(verts[near], rho[near], cam) + bf.splats_perspective_bruteforce(
+        verts[~near], 36, 30, cam["eye"], cam["fwd"], cam["up"], 55.0, 1.0, N)
+    np.testing.assert_allclose(oracle.hybrid(pos, N, cam, r_near), ref, rtol=1e-10, atol=1e-12)
+
+
+def test_perspective_splats_keep_the_projected_mass():
+    """A perspective splat carries m |dir| / Z^2 over the image plane (at unit
+    distance), like the exact projection of the same tetrahedron to leading
+    order in its size over its distance: the frame masses agree to about
+    (h / Z)^2."""
+    N = 8
+    pos = ZeldovichField.generate(N, -2.0, 3.0, 23).positions(1.0)
+    cam = camera_dict("persp", 96, 96, eye=(0.5, -2.0, 0.5), fwd=(0, 1, 0), up=(0, 0, 1), fov_y_deg=40)
+    exact = oracle.render(pos, N, cam).sum()
+    splat = oracle.centroids(pos, N, cam).sum()
+    assert abs(splat / exact - 1.0) <= 3e-3
