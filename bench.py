@@ -53,7 +53,13 @@ def parse():
     ap.add_argument("--frames", type=int, default=0, help="override frame count (debug)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-atomic", action="store_true")
+    ap.add_argument("--no-resample", action="store_true")
+    ap.add_argument("--one-frame", action="store_true",
+                    help="profiling case: bin frame 0 of the workload (snapshot 0, camera 0) and render it three "
+                         "times with --tile; prints a summary instead of the JSON line")
+    ap.add_argument("--tile", type=int, default=32)
     ap.add_argument("--cpu-sample-crop", type=int, default=384)
+    ap.add_argument("--oracle-crop", type=int, default=256, help="crop edge of the atomic form's oracle check")
     return ap.parse_args()
 
 
@@ -248,6 +254,7 @@ def run_lt(args, rank: int, world: int):
     # the same exact path) on every 8th frame, against the tiled form on the
     # same frames
     atomic = None
+    atomic_crops = []
     if not args.no_atomic:
         sub = list(range(0, F, 8))
         sub_cams, sub_snaps = [cams[q] for q in sub], [snaps[q] for q in sub]
@@ -278,8 +285,21 @@ def run_lt(args, rank: int, world: int):
         atomic = {"value": sub_frags / (a_ms * 1e-3), "unit": "fragments/s", "frames": len(sub),
                   "ms": a_ms, "tiled_ms_same_frames": b_ms, "speedup_tiled_over_atomic": a_ms / b_ms,
                   "max_rel_diff_vs_tiled": rel}
+        # central crops of four of these frames from both forms, for the CPU
+        # leg's comparison with the oracle
+        for q in (0, 5, 10, 14):
+            if q < len(sub):
+                x0c, y0c, wc, hc = central_crop(cams[sub[q]], args.oracle_crop)
+                atomic_crops.append((sub[q], a_img[q, y0c:y0c + hc, x0c:x0c + wc].cpu().numpy(),
+                                     t_img[q, y0c:y0c + hc, x0c:x0c + wc].cpu().numpy()))
         del a_img, t_img
         R.sync()
+
+    # resampling onto a periodic grid (the next row of the path): the 128^3
+    # lattice onto 512^3 cells, density weighting
+    resample = None if args.no_resample else bench_resample(dev)
+    if resample is not None:
+        log(f"resample: {resample['ms']:.1f} ms")
 
     # max over ranks
     if world > 1:
@@ -352,11 +372,74 @@ def run_lt(args, rank: int, world: int):
     }
     if atomic is not None:
         line["atomic"] = atomic
+    if resample is not None:
+        line["resample"] = resample
     # the GPU's pixels of frame 0's central crop (from the last end-to-end
     # step's host copy), for the parity figure next to the CPU baseline
     x0c, y0c, wc, hc = central_crop(cams[0], args.cpu_sample_crop)
     gpu_crop = host_img[0, y0c:y0c + hc, x0c:x0c + wc].numpy().copy()
-    return line, (c, pos_np, cams, snaps, gpu_crop)
+    return line, (c, pos_np, cams, snaps, gpu_crop, atomic_crops)
+
+
+# FP64 operations the resampling counts (FMA as 2, division as 1): per
+# (tetrahedron, line) interval, four face planes (two FMA and a division
+# each) and four min/max; per piece of an interval in one slab, a max, a min,
+# a subtraction and two multiplications.
+RESAMPLE_FLOPS_PER_INTERVAL = 24
+RESAMPLE_FLOPS_PER_PIECE = 5
+# GB300 FP64 peak (nominal; there is no measured FP64 figure for this machine)
+FP64_PEAK_TFLOPS = 1.25
+
+
+def bench_resample(dev, n: int = 512, reps: int = 3):
+    """Time lt_resample of the 128^3 workload (deformation eigenvalue 3) onto
+    a periodic n^3 grid, density weighting, with CUDA events; report the
+    (tetrahedron, line) intervals per second and the FP64 roofline."""
+    import torch
+
+    from lt_inputs import ZeldovichField, config
+    from paper_1208_3206_gb300.render import Renderer
+
+    c = config("zel128_ortho1024")
+    N = c["N"]
+    pos = torch.from_numpy(ZeldovichField.generate(N, c["n_index"], c["k_cut"], c["seed"]).positions(c["lams"][0]))
+    R = Renderer()
+    R.build_tets(pos.to(dev), N)
+    grid = torch.empty((n, n, n), dtype=torch.float32, device=dev)
+    R.resample(n, "density", out=grid)  # warm-up (sizes the bins)
+    R.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        R.resample(n, "density", out=grid)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    st = R.get_stats()
+    # its bin pass alone (the same orthographic view of the grid's columns),
+    # to time the resampling kernels without it
+    from lt_inputs import ortho_z
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record()
+    for _ in range(reps):
+        R.project_bin([ortho_z(n, n)])
+    b1.record()
+    torch.cuda.synchronize()
+    bin_ms = b0.elapsed_time(b1) / reps
+    R.close()
+    kernel_ms = max(ms - bin_ms, 1e-6)
+    iv, pc = st["resample_intervals"], st["resample_pieces"]
+    flops = RESAMPLE_FLOPS_PER_INTERVAL * iv + RESAMPLE_FLOPS_PER_PIECE * pc
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    return {"workload": f"zel128 lattice (12.6M tetrahedra) onto {n}^3 cells, density weighting",
+            "ms": ms, "value": iv / (ms * 1e-3), "unit": "intervals/s", "intervals": iv, "pieces": pc,
+            "cells_per_s": n ** 3 / (ms * 1e-3), "bin_ms": bin_ms, "kernel_ms": kernel_ms,
+            "timing": "ms: the whole call, with its bin pass (one host synchronisation); kernel_ms: ms - bin_ms",
+            "roofline": {"bound": "alu", "kernel": "k_resample (FP64 clipping)", "achieved": achieved,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "counted": f"{RESAMPLE_FLOPS_PER_INTERVAL} FP64 flops per interval + "
+                                    f"{RESAMPLE_FLOPS_PER_PIECE} per slab piece",
+                         "peak_from": "GB300 nominal FP64 rate"}}
 
 
 def e2e_pipelined(pos, host_pos, img, host_img, N, cams, snaps, cfg, steps, barrier):
@@ -552,8 +635,39 @@ def run_reference(args, rank: int, world: int):
     }
 
 
+def one_frame(args):
+    """A small case for profiler captures: the first frame of the workload
+    (its snapshot alone on the device), binned once and rendered three
+    times with a fixed tile and 128-thread CTAs."""
+    import torch
+
+    from lt_inputs import ZeldovichField, config, ortho_z, sphere_cameras
+    from paper_1208_3206_gb300.render import Renderer
+
+    c = config(args.workload)
+    N = c["N"]
+    pos = ZeldovichField.generate(N, c["n_index"], c["k_cut"], c["seed"]).positions(c["lams"][0])
+    if c["view"] == "sphere16":
+        cam = sphere_cameras(16, c["W"], c["H"], radius=c["radius"], fov_y_deg=c["fov_y_deg"])[0]
+    else:
+        cam = ortho_z(c["W"], c["H"])
+    R = Renderer(tile=args.tile, raster_threads=128)
+    R.build_tets(torch.from_numpy(pos).cuda(), N)
+    R.project_bin([cam])
+    img = R.render_tiles()
+    for _ in range(2):
+        R.render_tiles(image=img)
+    R.sync()
+    st = R.get_stats()
+    print(f"one frame of {args.workload}: tile {args.tile}, {st['entries']} bin entries, "
+          f"{st['exact_fragments']} exact fragments over 3 renders, image sum {float(img.double().sum()):.6f}")
+
+
 def main():
     args = parse()
+    if args.one_frame:
+        one_frame(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
@@ -571,8 +685,20 @@ def main():
     line, wl = run_lt(args, rank, world)
     if rank == 0 and not args.no_cpu_baseline:
         log("CPU oracle sample")
-        c, pos_np, cams, snaps, gpu_crop = wl
+        c, pos_np, cams, snaps, gpu_crop, atomic_crops = wl
         line["cpu_baseline"], line["parity"] = cpu_baseline(c, pos_np, cams, snaps, args.cpu_sample_crop, gpu_crop)
+        if atomic_crops and "atomic" in line:
+            # both forms against the oracle on the same central crops
+            a_err, t_err = 0.0, 0.0
+            for fr, a_crop, t_crop in atomic_crops:
+                _, _, ref = oracle_sample(c, pos_np, cams, snaps, args.oracle_crop, fr)
+                a_err = max(a_err, crop_parity(ref, a_crop)["max_rel_err"])
+                t_err = max(t_err, crop_parity(ref, t_crop)["max_rel_err"])
+            line["atomic"]["err_vs_oracle"] = a_err
+            line["atomic"]["tiled_err_vs_oracle"] = t_err
+            line["atomic"]["err_sample"] = (f"central {args.oracle_crop}^2 crops of frames "
+                                            f"{[fr for fr, _, _ in atomic_crops]}: max |GPU - oracle| / "
+                                            f"max(pixel, mean of the crop), tolerance 1e-4")
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:

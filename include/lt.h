@@ -68,6 +68,7 @@ typedef enum {
 } lt_status;
 
 typedef enum { LT_POS_F32X4 = 0, LT_POS_F16_OFFSETS = 1 } lt_pos_format;
+typedef enum { LT_WEIGHT_DENSITY = 0, LT_WEIGHT_STREAMS = 1 } lt_resample_weight;
 typedef enum { LT_ORTHO = 0, LT_PERSP = 1 } lt_camera_type;
 
 /* One view. right = normalize(up x fwd), up' = fwd x right.
@@ -91,6 +92,11 @@ typedef struct {
   double hi[2];
   int W, H;
   int wrap;
+  /* hybrid near/far rendering (perspective only, 0 = off): with r > 0 the
+   * exact raster (lt_project_bin, lt_render_tiles, graphs) draws only the
+   * cubes whose corner-0 particle lies within r of the eye, and
+   * lt_render_centroids only the others; lt_render_hybrid draws both */
+  double near_radius;
 } lt_camera;
 
 /* Tuning knobs (lt_autotune fills them; zero fields take defaults). */
@@ -115,7 +121,9 @@ typedef struct {
   long long behind_eye;      /* cubes skipped because they straddle a perspective eye plane */
   long long range_overflow;  /* pixels that left the accumulator range */
   long long exact_fragments; /* ill-conditioned fragments re-evaluated in FP64 (cumulative) */
-  long long queue_overflow;  /* such fragments left in FP32 because a CTA's queue (32768 per tile) was full */
+  long long queue_overflow;  /* such fragments left in FP32 because a CTA's queue (32 per pixel of a tile) was full */
+  long long resample_intervals; /* lt_resample: (tetrahedron, grid line) pairs of positive length, last call */
+  long long resample_pieces;    /* lt_resample: their pieces in separate slabs (cell adds), last call */
   int n_frames;              /* frames of the last lt_project_bin */
   int tile;                  /* tile edge in use */
   int graph_kernels;         /* kernel nodes in the graph of the last lt_graph_build */
@@ -221,6 +229,94 @@ lt_status lt_count_fragments(lt_ctx* ctx, long long* h_counts, lt_stream stream)
 lt_status lt_render_backward(lt_ctx* ctx, const float* d_dL_dimage, float* d_dL_dpos, lt_stream stream);
 
 /*
+ * lt_resample -- resampling onto a periodic grid (Sec. 4.3, Eq. 10-12) and
+ * the stream-count field (Sec. 3.2).
+ * For snapshot `snapshot` of the registered lattice, fills d_grid (float
+ * [n][n][n], index (c n + b) n + a, caller owned) with, for every cell
+ * (a, b, c) of edge g = box / n, the sum over tetrahedra t of q_t times the
+ * length of the part of the cell's central line along z, x = (a + 1/2) g,
+ * y = (b + 1/2) g, that lies inside t and inside the slab [c g, (c + 1) g)
+ * (every periodic copy of t counts). weight LT_WEIGHT_DENSITY: q_t = rho_t
+ * (Eq. 3), so a cell holds rho dl, its mass over its face area;
+ * LT_WEIGHT_STREAMS: q_t = 1, so a cell over g is the mean number of streams
+ * on its line. Each (tetrahedron, line) interval is found exactly in FP64 by
+ * clipping the line against the four face planes; the cells are summed as
+ * 64-bit fixed-point integers (2^-frac_bits of the mean cell), so the grid
+ * is bitwise reproducible. Tetrahedra with V == 0 contribute nothing.
+ * Uses the project-and-bin pass with an orthographic view along z whose
+ * pixels are the grid's columns, so it replaces the frames and bins of the
+ * last lt_project_bin (render or count afterwards only after a new
+ * lt_project_bin), synchronises once to size the bins, and keeps an n^3
+ * array of 64-bit cells in the context.
+ * Errors: LT_ERR_STATE (no lt_build_tets), LT_ERR_ARG (null d_grid, n < 1 or
+ * n > 2048, unknown weight, snapshot out of range), LT_ERR_NOMEM; a cell
+ * leaving the fixed-point range latches LT_ERR_RANGE.
+ */
+lt_status lt_resample(lt_ctx* ctx, int n, int weight, int snapshot, float* d_grid, lt_stream stream);
+
+/*
+ * lt_slice -- a 2D slice of the total density of overlapping streams (Sec.
+ * 3.2, Eq. 4) or of the number of streams, on the plane z = z0 of the
+ * periodic box.
+ * For snapshot `snapshot` of the registered lattice, fills d_img (float
+ * [n][n], index b n + a, caller owned) with, at the point
+ * ((a + 1/2) box / n, (b + 1/2) box / n, z0), the sum over the tetrahedra
+ * that contain it (every periodic copy counts) of rho_t = m / |V_t|
+ * (LT_WEIGHT_DENSITY: the total density) or of 1 (LT_WEIGHT_STREAMS: the
+ * number of streams). The containment test is done in FP64 against the four
+ * face planes; a point on a face counts for both tetrahedra sharing it.
+ * Sums are 64-bit fixed point in units of 2^-frac_bits of the mean density
+ * (of one stream: counts are exact), so the slice is bitwise reproducible.
+ * Tetrahedra with V == 0 contribute nothing. Asynchronous; leaves the bins
+ * of the last lt_project_bin untouched; keeps an n^2 array of 64-bit sums in
+ * the context.
+ * Errors: LT_ERR_STATE (no lt_build_tets), LT_ERR_ARG (null d_img, n < 1 or
+ * n > 32768, unknown weight, z0 not finite, snapshot out of range),
+ * LT_ERR_NOMEM; a point leaving the fixed-point range latches LT_ERR_RANGE.
+ */
+lt_status lt_slice(lt_ctx* ctx, int n, int weight, int snapshot, double z0, float* d_img, lt_stream stream);
+
+/*
+ * lt_render_centroids -- the centroid rendering of Sec. 4.2 for one view:
+ * every tetrahedron of snapshot `snapshot` is drawn as a 2D kernel on a
+ * billboard through its centroid c_T = (v0 + v1 + v2 + v3) / 4, facing the
+ * view direction, scaled with (m / rho_T)^(1/3) = |V_T|^(1/3) and carrying
+ * the tetrahedron's mass m. The paper leaves the kernel's form and the scale
+ * factor open; this library takes the 2D M4 cubic spline with unit integral
+ * and smoothing length h = |V_T|^(1/3) (support radius 2h). A pixel (centre
+ * sample) adds m W(d, h) for each billboard its ray crosses, d the distance
+ * of the crossing from the centroid, over the cosine of the ray's angle to
+ * the view direction (1 for orthographic views): an estimate of the column
+ * density. Perspective billboards behind the eye are not drawn; a periodic
+ * orthographic window draws every periodic copy. With cam->near_radius > 0
+ * only the cubes beyond it are drawn (the far part of lt_render_hybrid).
+ * Pixels are summed as 64-bit fixed-point integers (2^-frac_bits of the mean
+ * column density), so the image is bitwise reproducible. Tetrahedra with
+ * V == 0 carry no splat.
+ * d_image: float [H][W] (caller owned, overwritten). Synchronises (the view
+ * is staged through the context's pinned memory); keeps an H x W array of
+ * 64-bit sums in the context; leaves the bins of lt_project_bin untouched.
+ * Errors: LT_ERR_STATE (no lt_build_tets), LT_ERR_ARG (null pointer,
+ * invalid camera, snapshot out of range), LT_ERR_NOMEM; a pixel leaving the
+ * fixed-point range latches LT_ERR_RANGE.
+ */
+lt_status lt_render_centroids(lt_ctx* ctx, const lt_camera* cam, int snapshot, float* d_image, lt_stream stream);
+
+/*
+ * lt_render_hybrid -- hybrid near/far rendering of one perspective view
+ * (Sec. 6, Fig. "LargeScale"): the cubes whose corner-0 particle lies within
+ * near_radius (> 0) of the eye are drawn by the exact projection of Eq. 6
+ * (lt_project_bin + lt_render_tiles), the other cubes' tetrahedra as
+ * centroid splats (lt_render_centroids); d_image (float [H][W], caller
+ * owned) receives the sum. Replaces the frames and bins of the last
+ * lt_project_bin; synchronises.
+ * Errors: as lt_project_bin and lt_render_centroids; LT_ERR_ARG for an
+ * orthographic view or near_radius <= 0.
+ */
+lt_status lt_render_hybrid(lt_ctx* ctx, const lt_camera* cam, int snapshot, double near_radius, float* d_image,
+                           lt_stream stream);
+
+/*
  * lt_graph_build / lt_graph_launch -- capture lt_project_bin followed by
  * lt_render_tiles for the given frames into a CUDA graph owned by the
  * context, and replay it. lt_graph_build runs the pass once uncaptured to
@@ -239,7 +335,8 @@ lt_status lt_graph_launch(lt_ctx* ctx, lt_stream stream);
 
 /*
  * lt_autotune -- time lt_project_bin + lt_render_tiles for the given
- * frames over a small grid of tile sizes and raster CTA shapes (CUDA
+ * frames over a small grid of tile sizes (16, 32, 64) and raster CTA shapes
+ * (128, 256 threads) (CUDA
  * events, `reps` timed repetitions each after one warm-up), keep the
  * fastest in the context and report it in *best (may be NULL).
  * Synchronises. d_image: scratch float [n_frames][H][W].

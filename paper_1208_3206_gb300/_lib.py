@@ -22,6 +22,7 @@ class LtCamera(C.Structure):
         ("W", C.c_int),
         ("H", C.c_int),
         ("wrap", C.c_int),
+        ("near_radius", C.c_double),
     ]
 
 
@@ -47,6 +48,8 @@ class LtStats(C.Structure):
         ("range_overflow", C.c_longlong),
         ("exact_fragments", C.c_longlong),
         ("queue_overflow", C.c_longlong),
+        ("resample_intervals", C.c_longlong),
+        ("resample_pieces", C.c_longlong),
         ("n_frames", C.c_int),
         ("tile", C.c_int),
         ("graph_kernels", C.c_int),
@@ -72,6 +75,7 @@ EXPORTS = [
     "lt_create", "lt_destroy", "lt_set_config", "lt_get_config", "lt_build_tets", "lt_project_bin",
     "lt_render_tiles", "lt_render_atomic", "lt_count_fragments", "lt_render_backward", "lt_graph_build",
     "lt_graph_launch", "lt_autotune", "lt_sync", "lt_get_stats", "lt_status_str", "lt_frame_mass_static",
+    "lt_resample", "lt_slice", "lt_render_centroids", "lt_render_hybrid",
 ]
 
 
@@ -135,6 +139,10 @@ def load(build_if_missing: bool = False):
         "lt_get_stats": ([vp, C.POINTER(LtStats)], C.c_int),
         "lt_status_str": ([C.c_int], C.c_char_p),
         "lt_frame_mass_static": ([vp, C.c_int, C.c_int, C.c_int, C.c_double, vp, vp], C.c_int),
+        "lt_resample": ([vp, C.c_int, C.c_int, C.c_int, vp, vp], C.c_int),
+        "lt_slice": ([vp, C.c_int, C.c_int, C.c_int, C.c_double, vp, vp], C.c_int),
+        "lt_render_centroids": ([vp, cam_p, C.c_int, vp, vp], C.c_int),
+        "lt_render_hybrid": ([vp, cam_p, C.c_int, C.c_double, vp, vp], C.c_int),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)

@@ -63,6 +63,17 @@ struct lt_ctx {
   // zero-volume tetrahedra: one bit per tetrahedron, a byte per (snapshot, cube)
   unsigned char* d_degen = nullptr;
   size_t degen_cap = 0;
+  // resampling: fixed-point cells
+  unsigned long long* d_racc = nullptr;
+  size_t racc_cap = 0;
+  // slices: fixed-point points
+  unsigned long long* d_sacc = nullptr;
+  size_t sacc_cap = 0;
+  // centroid splats: the frame and fixed-point pixels
+  FrameDev* d_frame_cen = nullptr;
+  size_t frame_cen_cap = 0;
+  unsigned long long* d_cacc = nullptr;
+  size_t cacc_cap = 0;
   // backward
   float* d_corner_grad = nullptr;
   size_t corner_grad_cap = 0;
@@ -202,6 +213,8 @@ void split_affine(double base, double gi, double gj, double gk, int N, float* h,
 bool make_frame(const lt_camera& c, const lt_ctx* ctx, int snapshot, int tile, int frame_index, FrameDev& F) {
   if (c.type != LT_ORTHO && c.type != LT_PERSP) return false;
   if (c.W < 1 || c.H < 1 || c.W > 65536 || c.H > 65536) return false;
+  // hybrid near/far rendering: perspective views only
+  if (!(c.near_radius >= 0.0) || !(c.near_radius < 1e150) || (c.near_radius > 0.0 && c.type != LT_PERSP)) return false;
   double f[3] = {c.fwd[0], c.fwd[1], c.fwd[2]}, up[3] = {c.up[0], c.up[1], c.up[2]};
   if (!(f[0] * f[0] + f[1] * f[1] + f[2] * f[2] > 0)) return false;
   norm3(f);
@@ -291,6 +304,7 @@ bool make_frame(const lt_camera& c, const lt_ctx* ctx, int snapshot, int tile, i
   }
   F.m_tet = m;
   F.sigma_units = (float)scale_bits;
+  F.near_r2 = c.near_radius > 0.0 ? c.near_radius * c.near_radius : 0.0;
   return true;
 }
 
@@ -374,7 +388,8 @@ lt_status ensure_tiles(lt_ctx* ctx, long long n) {
   }
   const size_t words = lt::scan_tmp_words(n);
   if ((st = grow_c(ctx, &ctx->d_scan_tmp, &ctx->scan_tmp_cap, words)) != LT_OK) return st;
-  const size_t xq = (size_t)ctx->num_sms * lt::kRasterMaxCtasPerSm * lt::kExactQueueCap;
+  const size_t xq = (size_t)ctx->num_sms * lt::kRasterMaxCtasPerSm * lt::kExactQueuePerPixel * ctx->cfg.tile *
+                    ctx->cfg.tile;
   if ((st = grow_c(ctx, &ctx->d_xq, &ctx->xq_cap, xq)) != LT_OK) return st;
   return LT_OK;
 }
@@ -432,7 +447,7 @@ lt_status render_impl(lt_ctx* ctx, float* d_image, double* d_mass, cudaStream_t 
   a.ctr = ctx->d_ctr;
   a.tile = ctx->tile;
   a.xq = ctx->d_xq;
-  a.xq_cap = lt::kExactQueueCap;
+  a.xq_cap = lt::kExactQueuePerPixel * (unsigned)(ctx->tile * ctx->tile);
   a.list_cap = ctx->list_cap;
   const int threads = ctx->cfg.raster_threads;
   int cps = ctx->cfg.ctas_per_sm;
@@ -448,6 +463,27 @@ lt_status render_impl(lt_ctx* ctx, float* d_image, double* d_mass, cudaStream_t 
   if (d_mass) {
     LT_CUDA(lt::launch_mass_reduce(ctx->d_mass_tile, ctx->n_tiles / ctx->n_frames, ctx->n_frames, d_mass, s));
   }
+  return LT_OK;
+}
+
+// Centroid splats of one view into d_image (overwritten, or added to when
+// `add`): the frame staged through the pinned memory (the call waits for
+// the copy to leave it, since the staging is shared with the other entry
+// points), 64-bit fixed-point sums in the context.
+lt_status centroids_impl(lt_ctx* ctx, const lt_camera& cam, int snapshot, float* d_image, bool add, cudaStream_t s) {
+  FrameDev F;
+  if (!make_frame(cam, ctx, snapshot, ctx->cfg.tile, 0, F)) return LT_ERR_ARG;
+  lt_status st = grow(&ctx->d_frame_cen, &ctx->frame_cen_cap, 1);
+  if (st != LT_OK) return st;
+  const size_t np = (size_t)cam.W * cam.H;
+  if ((st = grow(&ctx->d_cacc, &ctx->cacc_cap, np)) != LT_OK) return st;
+  if ((st = grow_pinned(&ctx->h_frames, &ctx->h_frames_cap, 1)) != LT_OK) return st;
+  ctx->h_frames[0] = F;
+  LT_CUDA(cudaMemcpyAsync(ctx->d_frame_cen, ctx->h_frames, sizeof(FrameDev), cudaMemcpyHostToDevice, s));
+  // the fixed-point unit is the frame's: 2^-frac_bits of its mean column density
+  LT_CUDA(lt::launch_centroids(ctx->L, ctx->d_frame_cen, cam.W, cam.H, F.m_tet, F.unit, ctx->d_cacc, d_image, add,
+                               ctx->d_ctr, s));
+  LT_CUDA(cudaStreamSynchronize(s));
   return LT_OK;
 }
 
@@ -520,6 +556,10 @@ void lt_destroy(lt_ctx* ctx) {
   cudaFree(ctx->d_ctr);
   cudaFree(ctx->d_frag);
   cudaFree(ctx->d_corner_grad);
+  cudaFree(ctx->d_racc);
+  cudaFree(ctx->d_sacc);
+  cudaFree(ctx->d_frame_cen);
+  cudaFree(ctx->d_cacc);
   cudaFree(ctx->d_degen);
   if (ctx->h_ctr) cudaFreeHost(ctx->h_ctr);
   if (ctx->h_u64) cudaFreeHost(ctx->h_u64);
@@ -651,6 +691,84 @@ lt_status lt_render_backward(lt_ctx* ctx, const float* d_dL_dimage, float* d_dL_
   return LT_OK;
 }
 
+lt_status lt_resample(lt_ctx* ctx, int n, int weight, int snapshot, float* d_grid, lt_stream stream) {
+  if (!ctx || !d_grid || n < 1 || n > 2048 || (weight != LT_WEIGHT_DENSITY && weight != LT_WEIGHT_STREAMS))
+    return LT_ERR_ARG;
+  if (!ctx->have_lattice) return LT_ERR_STATE;
+  if (snapshot < 0 || snapshot >= ctx->n_snap) return LT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the grid's columns are the pixels of an orthographic view along z over
+  // the periodic box window: pixel (a, b) is centred on column (a, b)
+  lt_camera cam;
+  memset(&cam, 0, sizeof cam);
+  cam.type = LT_ORTHO;
+  cam.fwd[2] = 1.0;
+  cam.up[1] = 1.0;
+  cam.hi[0] = cam.hi[1] = ctx->L.box;
+  cam.W = cam.H = n;
+  cam.wrap = 1;
+  const int snaps[1] = {snapshot};
+  lt_status st = project_bin_impl(ctx, &cam, 1, snaps, s, false);
+  if (st != LT_OK) return st;
+  const size_t cells = (size_t)n * n * n;
+  if ((st = grow(&ctx->d_racc, &ctx->racc_cap, cells)) != LT_OK) return st;
+  const double box = ctx->L.box, gs = box / n;
+  const int N = ctx->L.N;
+  const double m_tet = ctx->total_mass / (6.0 * (double)N * N * N);
+  // fixed-point unit: 2^-frac_bits of the mean cell (mean density times g,
+  // or one stream times g)
+  const double mean_cell = weight == LT_WEIGHT_DENSITY ? ctx->total_mass / (box * box * box) * gs : gs;
+  const double unit = mean_cell / ldexp(1.0, ctx->cfg.frac_bits);
+  LT_CUDA(cudaMemsetAsync(&ctx->d_ctr->resample_intervals, 0, 2 * sizeof(unsigned long long), s));
+  LT_CUDA(lt::launch_resample(ctx->L, ctx->d_frames, ctx->n_tiles, ctx->tile, ctx->d_off, ctx->d_list, ctx->list_cap,
+                              n, weight, m_tet, unit, ctx->d_racc, d_grid, ctx->d_ctr, s));
+  return LT_OK;
+}
+
+lt_status lt_slice(lt_ctx* ctx, int n, int weight, int snapshot, double z0, float* d_img, lt_stream stream) {
+  if (!ctx || !d_img || n < 1 || n > 32768 || (weight != LT_WEIGHT_DENSITY && weight != LT_WEIGHT_STREAMS) ||
+      !isfinite(z0))
+    return LT_ERR_ARG;
+  if (!ctx->have_lattice) return LT_ERR_STATE;
+  if (snapshot < 0 || snapshot >= ctx->n_snap) return LT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t np = (size_t)n * n;
+  lt_status st = grow(&ctx->d_sacc, &ctx->sacc_cap, np);
+  if (st != LT_OK) return st;
+  const double box = ctx->L.box;
+  const int N = ctx->L.N;
+  const double m_tet = ctx->total_mass / (6.0 * (double)N * N * N);
+  // fixed-point unit: 2^-frac_bits of the mean density, or of one stream
+  const double scale = weight == LT_WEIGHT_DENSITY ? ctx->total_mass / (box * box * box) : 1.0;
+  const double unit = scale / ldexp(1.0, ctx->cfg.frac_bits);
+  LT_CUDA(lt::launch_slice(ctx->L, snapshot, n, weight, z0, m_tet, unit, ctx->d_sacc, d_img, ctx->d_ctr, s));
+  return LT_OK;
+}
+
+lt_status lt_render_centroids(lt_ctx* ctx, const lt_camera* cam, int snapshot, float* d_image, lt_stream stream) {
+  if (!ctx || !cam || !d_image) return LT_ERR_ARG;
+  if (!ctx->have_lattice) return LT_ERR_STATE;
+  if (snapshot < 0 || snapshot >= ctx->n_snap) return LT_ERR_ARG;
+  return centroids_impl(ctx, *cam, snapshot, d_image, false, (cudaStream_t)stream);
+}
+
+lt_status lt_render_hybrid(lt_ctx* ctx, const lt_camera* cam, int snapshot, double near_radius, float* d_image,
+                           lt_stream stream) {
+  if (!ctx || !cam || !d_image) return LT_ERR_ARG;
+  if (!ctx->have_lattice) return LT_ERR_STATE;
+  if (snapshot < 0 || snapshot >= ctx->n_snap || cam->type != LT_PERSP || !(near_radius > 0.0)) return LT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  lt_camera c = *cam;
+  c.near_radius = near_radius;
+  const int snaps[1] = {snapshot};
+  // the near cubes: exact projection
+  lt_status st = project_bin_impl(ctx, &c, 1, snaps, s, false);
+  if (st != LT_OK) return st;
+  if ((st = render_impl(ctx, d_image, nullptr, s)) != LT_OK) return st;
+  // the far cubes: centroid splats, added to the image
+  return centroids_impl(ctx, c, snapshot, d_image, true, s);
+}
+
 lt_status lt_graph_build(lt_ctx* ctx, const lt_camera* cams, int n_frames, const int* frame_snapshot,
                          float* d_image, double* d_mass, lt_stream stream) {
   if (!ctx || !d_image) return LT_ERR_ARG;
@@ -717,7 +835,7 @@ lt_status lt_autotune(lt_ctx* ctx, const lt_camera* cams, int n_frames, const in
   if (!ctx->have_lattice) return LT_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   const lt_config base = ctx->cfg;
-  const int tiles[] = {16, 32};
+  const int tiles[] = {16, 32, 64};
   const int threads[] = {128, 256};
   float best_ms = 1e30f;
   lt_config best_cfg = base;
@@ -783,6 +901,8 @@ lt_status lt_get_stats(lt_ctx* ctx, lt_stats* out) {
   out->range_overflow = (long long)c.range_overflow;
   out->exact_fragments = (long long)c.exact_fragments;
   out->queue_overflow = (long long)c.queue_overflow;
+  out->resample_intervals = (long long)c.resample_intervals;
+  out->resample_pieces = (long long)c.resample_pieces;
   out->n_frames = ctx->n_frames;
   out->tile = ctx->tile;
   out->graph_kernels = ctx->graph_kernels;

@@ -124,7 +124,8 @@ __global__ void __launch_bounds__(256) k_bin(Lattice L, const FrameDev* __restri
           have = true;
         }
       } else {
-        have = cube_tiles(L, F, cube, ct, finite_ok, behind);
+        // hybrid rendering: far cubes are drawn as splats, not binned
+        have = !cube_far(L, F, cube) && cube_tiles(L, F, cube, ct, finite_ok, behind);
         if (!SCATTER && fdesc) fdesc[cube] = encode_tiles(have, ct);
       }
     }

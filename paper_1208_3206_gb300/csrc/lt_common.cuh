@@ -70,6 +70,8 @@ struct DevCounters {
   unsigned long long total_entries;
   unsigned long long exact_fragments;  // fragments re-evaluated in FP64
   unsigned long long queue_overflow;   // ill-conditioned fragments kept in FP32 (queue full)
+  unsigned long long resample_intervals;  // (tetrahedron, grid line) pairs with a positive length
+  unsigned long long resample_pieces;     // their pieces in separate slabs
 };
 
 // Snapshot description.
@@ -158,6 +160,9 @@ struct FrameDev {
   double m_tet;           // mass of one tetrahedron
   float sigma_units;      // mean column density in accumulator units (2^frac_bits)
   float pad_;
+  // hybrid near/far rendering (perspective): when > 0, the square of the
+  // radius around the eye beyond which a cube counts as far (see cube_far)
+  double near_r2;
 };
 
 // ---------------------------------------------------------------------------
@@ -212,6 +217,34 @@ __device__ __forceinline__ float3 load_corner(const Lattice& L, long long snap_o
   const float3 d = load_disp(L, snap_off, i, j, k, n, ok);
   const int a = n & 1, b = (n >> 1) & 1, c = (n >> 2) & 1;
   return make_float3((float)a * L.h + d.x, (float)b * L.h + d.y, (float)c * L.h + d.z);
+}
+
+// Hybrid near/far rendering: a cube is far when its corner-0 particle
+// (unwrapped about its lattice point, in FP64) lies at least sqrt(near_r2)
+// from the eye; never when near_r2 == 0. Every kernel that splits by it
+// uses this one test, so each cube is drawn exactly once.
+__device__ __forceinline__ bool cube_far(const Lattice& L, const FrameDev& F, long long cube) {
+  if (!(F.near_r2 > 0.0)) return false;
+  const unsigned c = (unsigned)cube;
+  const int N = L.N;
+  const int i = (int)(c % (unsigned)N), j = (int)((c / (unsigned)N) % (unsigned)N), k = (int)(c / ((unsigned)N * N));
+  const float4 p = __ldg(reinterpret_cast<const float4*>(L.pos) + (long long)F.snapshot * L.n_particles + cube);
+  const double h = (double)L.box / N, box = (double)L.box;
+  const double pp[3] = {p.x, p.y, p.z};
+  const int ix[3] = {i, j, k};
+  // explicitly rounded operations (no fused multiply-add), so that the
+  // test rounds like a plain evaluation of the same expression
+  double e[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const double lq = __dmul_rn((double)ix[q], h);
+    double d = __dsub_rn(pp[q], lq);
+    if (d > 0.5 * box) d = __dsub_rn(d, box);
+    else if (d < -0.5 * box) d = __dadd_rn(d, box);
+    e[q] = __dsub_rn(__dadd_rn(lq, d), F.eyed[q]);
+  }
+  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1])), __dmul_rn(e[2], e[2]));
+  return !(r2 < F.near_r2);
 }
 
 // The eight corners of a cube projected to pixel coordinates, relative to
@@ -651,7 +684,10 @@ __device__ __forceinline__ void row_span(const TetRaster& t, const float* erow, 
 __device__ __forceinline__ void accum_fixed(unsigned long long* acc, float q, DevCounters* ctr) {
   constexpr float k2p63 = 9223372036854775808.0f;
   if (q < k2p63) {
-    const unsigned long long u = __float2ull_rn(q);
+    // values below 2^32 units (nearly all) convert through 32 bits: the
+    // 64-bit conversion runs on the FP64 pipe, which GB300 keeps narrow
+    const unsigned long long u =
+        q < 4294967040.0f ? (unsigned long long)__float2uint_rn(q) : __float2ull_rn(q);
     if (u) {
       const unsigned long long old = atomicAdd(acc, u);
       if (old > ~0ull - u) {
@@ -761,6 +797,65 @@ __device__ __noinline__ static double exact_fragment(const Lattice& L, const Fra
   const double chord = (t_out - t_in) * dl;
   const double val = m / fabs(V) * chord;
   return half ? val / dl : val;
+}
+
+// One tetrahedron in FP64, relative to its cube's corner-0 Lagrangian point.
+struct TetF64 {
+  double v[4][3];
+  double n[4][3];  // outward face normals (face f opposite vertex f)
+  double d[4];     // plane offsets: inside when n . p <= d
+  double V;        // signed volume (Eq. 9)
+};
+
+__device__ __forceinline__ void tet_f64(const Lattice& L, long long soff, int i, int j, int k, int s, bool& ok,
+                                        TetF64& t) {
+  const int N = L.N;
+  const double h = (double)L.box / N, box = (double)L.box;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int n = tet_corner_dyn(s, c);
+    const int a = n & 1, b = (n >> 1) & 1, cc = (n >> 2) & 1;
+    const int ii = i + a, jj = j + b, kk = k + cc;
+    const int im = ii == N ? 0 : ii, jm = jj == N ? 0 : jj, km = kk == N ? 0 : kk;
+    double dd[3];
+    if (L.fmt == 0) {
+      const float4 p = __ldg(reinterpret_cast<const float4*>(L.pos) + soff + particle_id(im, jm, km, N));
+      ok = ok && isfinite(p.x) && isfinite(p.y) && isfinite(p.z);
+      const double pp[3] = {p.x, p.y, p.z};
+      const int ix[3] = {im, jm, km};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        double e = pp[q] - ix[q] * h;  // minimum image of the displacement
+        if (e > 0.5 * box) e -= box;
+        else if (e < -0.5 * box) e += box;
+        dd[q] = e;
+      }
+    } else {
+      const float3 df = load_disp(L, soff, i, j, k, n, ok);
+      dd[0] = df.x; dd[1] = df.y; dd[2] = df.z;
+    }
+    t.v[c][0] = a * h + dd[0];
+    t.v[c][1] = b * h + dd[1];
+    t.v[c][2] = cc * h + dd[2];
+  }
+  const double e1[3] = {t.v[1][0] - t.v[0][0], t.v[1][1] - t.v[0][1], t.v[1][2] - t.v[0][2]};
+  const double e2[3] = {t.v[2][0] - t.v[0][0], t.v[2][1] - t.v[0][1], t.v[2][2] - t.v[0][2]};
+  const double e3[3] = {t.v[3][0] - t.v[0][0], t.v[3][1] - t.v[0][1], t.v[3][2] - t.v[0][2]};
+  t.V = (e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) + e1[1] * (e2[2] * e3[0] - e2[0] * e3[2]) +
+         e1[2] * (e2[0] * e3[1] - e2[1] * e3[0])) / 6.0;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const double* A = t.v[(f + 1) & 3];
+    const double* B = t.v[(f + 2) & 3];
+    const double* C = t.v[(f + 3) & 3];
+    const double u1[3] = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+    const double u2[3] = {C[0] - A[0], C[1] - A[1], C[2] - A[2]};
+    double nn[3] = {u1[1] * u2[2] - u1[2] * u2[1], u1[2] * u2[0] - u1[0] * u2[2], u1[0] * u2[1] - u1[1] * u2[0]};
+    const double side = nn[0] * (t.v[f][0] - A[0]) + nn[1] * (t.v[f][1] - A[1]) + nn[2] * (t.v[f][2] - A[2]);
+    if (side > 0.0) { nn[0] = -nn[0]; nn[1] = -nn[1]; nn[2] = -nn[2]; }
+    t.n[f][0] = nn[0]; t.n[f][1] = nn[1]; t.n[f][2] = nn[2];
+    t.d[f] = nn[0] * A[0] + nn[1] * A[1] + nn[2] * A[2];
+  }
 }
 
 // Error model of a fragment's FP32 value (accumulator units), with e its

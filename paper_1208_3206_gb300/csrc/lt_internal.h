@@ -46,13 +46,32 @@ struct RasterArgs {
 cudaError_t launch_raster(const RasterArgs& a, int ctas, int threads, int any_persp, cudaStream_t s);
 int raster_max_ctas_per_sm(int threads, int tile, int any_persp);
 constexpr int kRasterMaxCtasPerSm = 4;     // CTAs per SM the exact queue is sized for
-constexpr unsigned kExactQueueCap = 32768;  // queued fragments per CTA and tile
+constexpr unsigned kExactQueuePerPixel = 32;  // queued fragments per CTA and tile: 32 per pixel of the tile
 cudaError_t launch_count_fragments(const RasterArgs& a, unsigned long long* d_counts, int n_frames, int ctas,
                                    int threads, cudaStream_t s);
 cudaError_t launch_mass_reduce(const double* mass_tile, long long tpf, int n_frames, double* d_mass,
                                cudaStream_t s);
 cudaError_t launch_atomic(const Lattice& L, const FrameDev* d_frames, long long stride, int n_frames, float* image,
                           DevCounters* ctr, cudaStream_t s);
+
+// ---- lt_resample.cu: resampling onto a periodic n^3 grid (q = rho: weight 0,
+// q = 1: weight 1) from the bins of an orthographic view along z whose
+// pixels are the grid's columns.
+cudaError_t launch_resample(const Lattice& L, const FrameDev* d_frame, long long n_tiles, int tile,
+                            const unsigned long long* d_off, const unsigned* d_list, unsigned long long list_cap, int n,
+                            int weight, double m_tet, double unit, unsigned long long* d_acc, float* d_out,
+                            DevCounters* ctr, cudaStream_t s);
+
+// ---- lt_slice.cu: total density (weight 0) or stream count (weight 1) at
+// the centres of an n x n grid on the plane z = z0.
+cudaError_t launch_slice(const Lattice& L, int snapshot, int n, int weight, double z0, double m_tet, double unit,
+                         unsigned long long* d_acc, float* d_out, DevCounters* ctr, cudaStream_t s);
+
+// ---- lt_centroids.cu: centroid splats of one orthographic frame.
+// `add`: add to d_out instead of overwriting it. With F.near_r2 > 0 only
+// the far cubes (cube_far) are drawn.
+cudaError_t launch_centroids(const Lattice& L, const FrameDev* d_frame, int W, int H, double m_tet, double unit,
+                             unsigned long long* d_acc, float* d_out, bool add, DevCounters* ctr, cudaStream_t s);
 
 // ---- lt_backward.cu
 cudaError_t launch_backward(const Lattice& L, const FrameDev* d_frames, long long stride, int n_frames, int n_snap,

@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
           const unsigned long long li = e0 + (unsigned long long)cidx;
           const long long cube = LT_IN_BOUNDS(li < e1, &a.ctr->errors) ? (long long)a.list[li] : 0;
           zmask = a.L.degen ? (unsigned)__ldg(a.L.degen + snap_off + cube) & 63u : 0u;
+          if (cube_far(a.L, F, cube)) ok = false;  // hybrid rendering: drawn as splats
           int i, j, k;
           cube_ijk(a.L, cube, i, j, k);
           float X0 = 0.f, Y0 = 0.f, Z0 = 1.f;

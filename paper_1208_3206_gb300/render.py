@@ -34,6 +34,7 @@ class Camera:
     lo: Sequence[float] = (0.0, 0.0)
     hi: Sequence[float] = (1.0, 1.0)
     wrap: bool = False
+    near_radius: float = 0.0
 
     def to_c(self) -> LtCamera:
         c = LtCamera()
@@ -46,6 +47,7 @@ class Camera:
         c.hi[:] = [float(x) for x in self.hi]
         c.W, c.H = int(self.W), int(self.H)
         c.wrap = int(bool(self.wrap))
+        c.near_radius = float(self.near_radius)
         return c
 
 
@@ -190,6 +192,66 @@ class Renderer:
         check("lt_render_backward", self._lib.lt_render_backward(self._h, _ptr(g), _ptr(out), _stream()))
         return out
 
+    # -- lt_resample
+    def resample(self, n: int, weight: str = "density", snapshot: int = 0,
+                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Resampling of one registered snapshot onto a periodic n^3 grid
+        (float32 [n][n][n], index [c][b][a]): per cell, q dl along its
+        central line in z inside its slab, q = rho ("density") or 1
+        ("streams"). Replaces the frames and bins of the last project_bin."""
+        w = {"density": 0, "streams": 1}[weight]
+        if out is None:
+            out = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+        if out.dtype != torch.float32 or not out.is_cuda or out.numel() != n ** 3 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float32 CUDA tensor with n^3 elements")
+        check("lt_resample", self._lib.lt_resample(self._h, int(n), w, int(snapshot), _ptr(out), _stream()))
+        self._cams = []
+        return out
+
+    # -- lt_slice
+    def slice(self, n: int, z0: float, weight: str = "density", snapshot: int = 0,
+              out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Total density ("density") or number of streams ("streams") at the
+        centres of an n x n grid on the plane z = z0 (float32 [n][n], index
+        [b][a])."""
+        w = {"density": 0, "streams": 1}[weight]
+        if out is None:
+            out = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        if out.dtype != torch.float32 or not out.is_cuda or out.numel() != n * n or not out.is_contiguous():
+            raise ValueError("out must be a contiguous float32 CUDA tensor with n^2 elements")
+        check("lt_slice", self._lib.lt_slice(self._h, int(n), w, int(snapshot), float(z0), _ptr(out), _stream()))
+        return out
+
+    # -- lt_render_centroids
+    def render_centroids(self, cam, snapshot: int = 0, image: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Centroid splats (Sec. 4.2) of one registered snapshot in one
+        orthographic view: float32 [H][W]."""
+        cs, arr = _cams([cam])
+        c = cs[0]
+        if image is None:
+            image = torch.empty((c.H, c.W), dtype=torch.float32, device="cuda")
+        if image.dtype != torch.float32 or not image.is_cuda or image.numel() != c.H * c.W or not image.is_contiguous():
+            raise ValueError(f"image must be a contiguous float32 CUDA tensor with {c.H}x{c.W} elements")
+        check("lt_render_centroids", self._lib.lt_render_centroids(self._h, arr, int(snapshot), _ptr(image), _stream()))
+        return image
+
+    # -- lt_render_hybrid
+    def render_hybrid(self, cam, near_radius: float, snapshot: int = 0,
+                      image: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Hybrid near/far rendering of one perspective view: cubes within
+        near_radius of the eye by exact projection, the others as centroid
+        splats. float32 [H][W]."""
+        cs, arr = _cams([cam])
+        c = cs[0]
+        if image is None:
+            image = torch.empty((c.H, c.W), dtype=torch.float32, device="cuda")
+        if image.dtype != torch.float32 or not image.is_cuda or image.numel() != c.H * c.W or not image.is_contiguous():
+            raise ValueError(f"image must be a contiguous float32 CUDA tensor with {c.H}x{c.W} elements")
+        check("lt_render_hybrid", self._lib.lt_render_hybrid(self._h, arr, int(snapshot), float(near_radius),
+                                                             _ptr(image), _stream()))
+        self._cams = []
+        return image
+
     # -- graphs
     def graph_build(self, cams, frame_snapshot=None, image: Optional[torch.Tensor] = None,
                     mass: Optional[torch.Tensor] = None, stream: Optional[torch.cuda.Stream] = None):
@@ -245,6 +307,22 @@ def lt_render_tiles(r: Renderer, *a, **k):
 
 def lt_render_backward(r: Renderer, *a, **k):
     return r.render_backward(*a, **k)
+
+
+def lt_resample(r: Renderer, *a, **k):
+    return r.resample(*a, **k)
+
+
+def lt_slice(r: Renderer, *a, **k):
+    return r.slice(*a, **k)
+
+
+def lt_render_centroids(r: Renderer, *a, **k):
+    return r.render_centroids(*a, **k)
+
+
+def lt_render_hybrid(r: Renderer, *a, **k):
+    return r.render_hybrid(*a, **k)
 
 
 def lt_frame_mass_static(image: torch.Tensor, pixel_area: float, out: Optional[torch.Tensor] = None) -> torch.Tensor:
