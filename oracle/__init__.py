@@ -18,4 +18,5 @@ from .oracle import (  # noqa: F401
     point_density,
     centroids,
     hybrid,
+    render_area,
 )

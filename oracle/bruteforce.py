@@ -15,6 +15,10 @@ the oracle pins its arithmetic:
     barycentric inside test along each cell column.
   * `centroids_bruteforce`: the centroid splats of Sec. 4.2 over every
     (pixel, tetrahedron, period) triple, in numpy.
+  * `area_bruteforce`: area-averaged pixels of an orthographic view as the
+    volume of each tetrahedron clipped to the prism of each pixel's square
+    (the vertices of the eight-plane polytope by brute force over plane
+    triples, its volume by a convex hull), times rho, over the pixel's area.
 
 Both draw every periodic copy of every tetrahedron for periodic orthographic
 windows by brute force over image-period shifts in [-2, 2].
@@ -292,4 +296,67 @@ def splats_perspective_bruteforce(verts, W: int, H: int, eye, fwd, up, fov_y_deg
         q = d / h
         w = np.where(q < 1.0, 1.0 - 1.5 * q ** 2 + 0.75 * q ** 3, np.where(q < 2.0, 0.25 * (2.0 - q) ** 3, 0.0))
         out += m * 10.0 / (7.0 * math.pi * h * h) * w * np.sqrt(1.0 + XT ** 2 + YT ** 2)
+    return out
+
+
+def _clipped_volume(planes):
+    """Volume of {p : n . p <= d for all (n, d) in planes} (bounded), from
+    the feasible intersections of every plane triple."""
+    from itertools import combinations
+    from scipy.spatial import ConvexHull
+    from scipy.spatial import QhullError
+    n = np.array([q[0] for q in planes])
+    d = np.array([q[1] for q in planes])
+    pts = []
+    for a, b, c in combinations(range(len(planes)), 3):
+        M = n[[a, b, c]]
+        if abs(np.linalg.det(M)) < 1e-14:
+            continue
+        x = np.linalg.solve(M, d[[a, b, c]])
+        if np.all(n @ x <= d + 1e-12):
+            pts.append(x)
+    if len(pts) < 4:
+        return 0.0
+    try:
+        return float(ConvexHull(np.array(pts)).volume)
+    except QhullError:
+        return 0.0
+
+
+def area_bruteforce(pos, N: int, cam: dict, box: float = 1.0, total_mass: float = 1.0) -> np.ndarray:
+    """Area-averaged pixels [H][W] of an orthographic view: for every
+    (pixel, tetrahedron, period) triple, rho times the volume of the
+    tetrahedron inside the prism over the pixel's square, over the square's
+    area. Tiny inputs only."""
+    verts, rho, vol = lattice_tets(pos, N, box, total_mass)
+    r, u, _ = _frame(cam)
+    W, H = cam["W"], cam["H"]
+    lo, hi = np.asarray(cam["lo"], dtype=np.float64), np.asarray(cam["hi"], dtype=np.float64)
+    dx, dy = (hi[0] - lo[0]) / W, (hi[1] - lo[1]) / H
+    out = np.zeros((H, W))
+    for t in range(len(verts)):
+        if vol[t] == 0.0:
+            continue
+        v0 = verts[t]
+        for shift in _copies(cam):
+            v = v0 + shift
+            # outward face planes of the tetrahedron
+            faces = []
+            for f in range(4):
+                a, b, c = v[(f + 1) % 4], v[(f + 2) % 4], v[(f + 3) % 4]
+                nrm = np.cross(b - a, c - a)
+                if nrm @ (v[f] - a) > 0:
+                    nrm = -nrm
+                faces.append((nrm, float(nrm @ a)))
+            a_, b_ = v @ r, v @ u
+            x0 = max(0, int(math.floor((a_.min() - lo[0]) / dx)))
+            x1 = min(W - 1, int(math.floor((a_.max() - lo[0]) / dx)))
+            y0 = max(0, int(math.floor((b_.min() - lo[1]) / dy)))
+            y1 = min(H - 1, int(math.floor((b_.max() - lo[1]) / dy)))
+            for py in range(y0, y1 + 1):
+                for px in range(x0, x1 + 1):
+                    xa, xb = lo[0] + px * dx, lo[0] + (px + 1) * dx
+                    ya, yb = lo[1] + py * dy, lo[1] + (py + 1) * dy
+                    planes = faces + [(-r, -xa), (r, xb), (-u, -ya), (u, yb)]
+                    out[py, px] += rho[t] * _clipped_volume(planes) / (dx * dy)
     return out

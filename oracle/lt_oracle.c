@@ -19,6 +19,9 @@
  *   - the gradient of that projection with respect to particle positions,
  *     by differentiating rho_i * dl_i directly (density through the volume,
  *     chord through the entry and exit face planes).
+ *   - area-averaged pixels of orthographic views (orc_render_area): the
+ *     mean of Eq. 6 over each pixel's square, each tetrahedron's chord
+ *     integrated exactly over its piecewise-linear pieces.
  *
  * Readings where the paper is silent:
  *   - corner n of a cube is lattice point (i+(n&1), j+((n>>1)&1), k+((n>>2)&1));
@@ -30,6 +33,8 @@
  *   - orthographic windows may be periodic in both image axes (wrap), in
  *     which case every periodic copy of a tetrahedron is drawn; perspective
  *     views draw the single unwrapped copy of the lattice;
+ *   - an area-averaged pixel splits the window into W x H equal squares,
+ *     pixel (px, py) covering [px, px + 1) x [py, py + 1) in pixel units;
  *   - the tetrahedron is closed: a ray lying exactly in the plane of a face
  *     parallel to it counts the segment it shares with the face (the value
  *     there is the upper one-sided limit of a jump).
@@ -818,4 +823,190 @@ int orc_hybrid(const double* pos, int N, double box, double total_mass, const or
 int orc_centroids(const double* pos, int N, double box, double total_mass, const orc_camera* cam, double* out,
                   int nthreads) {
   return orc_hybrid(pos, N, box, total_mass, cam, 0.0, out, nthreads);
+}
+
+/*
+ * Area-averaged pixels (orthographic views): each pixel holds the mean of the
+ * column density (Eq. 6) over its square instead of the value at its
+ * centre. For one tetrahedron the chord dl(x, y) is zero on the boundary of
+ * the projected hull and linear on each triangle joining the apex -- the
+ * projected vertex inside the triangle of the other three, or else the
+ * crossing of the hull's two diagonals -- to a hull edge (the front and back
+ * faces change there and nowhere else). So the integral over the pixel
+ * square is, per triangle, the area of the triangle clipped to the square
+ * times dl at the clipped polygon's centroid. dl at the apex is the depth of
+ * the back surface minus that of the front one there. A periodic window
+ * draws every periodic copy. out: [H][W].
+ */
+typedef struct { double x, y; } pt2;
+
+/* Clip polygon p[n] (convex, counter-clockwise or not) to the half-plane
+ * s * (x - x0) >= 0 (axis 0) or s * (y - y0) >= 0 (axis 1); returns the new
+ * vertex count (at most n + 1). */
+static int clip_half(const pt2* p, int n, int axis, double x0, double s, pt2* q) {
+  int m = 0;
+  for (int i = 0; i < n; ++i) {
+    const pt2 a = p[i], b = p[(i + 1) % n];
+    const double da = s * ((axis == 0 ? a.x : a.y) - x0), db = s * ((axis == 0 ? b.x : b.y) - x0);
+    if (da >= 0.0) q[m++] = a;
+    if ((da >= 0.0) != (db >= 0.0)) {
+      const double t = da / (da - db);
+      q[m].x = a.x + t * (b.x - a.x);
+      q[m].y = a.y + t * (b.y - a.y);
+      ++m;
+    }
+  }
+  return m;
+}
+
+/* Integral over the square [x0, x1] x [y0, y1] of the linear function that is
+ * h at A and 0 at B and C, restricted to triangle ABC. */
+static double tri_square_integral(pt2 A, pt2 B, pt2 C, double h, double x0, double x1, double y0, double y1) {
+  pt2 p[8], q[8];
+  p[0] = A; p[1] = B; p[2] = C;
+  int n = 3;
+  n = clip_half(p, n, 0, x0, 1.0, q);
+  n = clip_half(q, n, 0, x1, -1.0, p);
+  n = clip_half(p, n, 1, y0, 1.0, q);
+  n = clip_half(q, n, 1, y1, -1.0, p);
+  if (n < 3) return 0.0;
+  double area2 = 0.0, cx = 0.0, cy = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const pt2 a = p[i], b = p[(i + 1) % n];
+    const double cr = a.x * b.y - b.x * a.y;
+    area2 += cr;
+    cx += (a.x + b.x) * cr;
+    cy += (a.y + b.y) * cr;
+  }
+  if (area2 == 0.0) return 0.0;
+  cx /= 3.0 * area2;
+  cy /= 3.0 * area2;
+  /* barycentric weight of A at the centroid */
+  const double den = (B.y - C.y) * (A.x - C.x) + (C.x - B.x) * (A.y - C.y);
+  if (den == 0.0) return 0.0;
+  const double la = ((B.y - C.y) * (cx - C.x) + (C.x - B.x) * (cy - C.y)) / den;
+  return 0.5 * fabs(area2) * h * la;
+}
+
+static double orient2(pt2 a, pt2 b, pt2 c) { return (b.x - a.x) * (c.y - a.y) - (b.y - a.y) * (c.x - a.x); }
+
+int orc_render_area(const double* pos, int N, double box, double total_mass, const orc_camera* cam, double* out,
+                    int nthreads) {
+  frame_t fr;
+  if (N <= 0 || box <= 0 || frame_init(cam, &fr) != ORC_OK || fr.persp) return ORC_ERR_ARG;
+  const long npix = (long)fr.W * fr.H;
+  const int T = num_threads(nthreads);
+  double* bufs = (double*)calloc((size_t)T * npix, sizeof(double));
+  const double m = total_mass / (6.0 * (double)N * N * N);
+  const double dx = (fr.hi[0] - fr.lo[0]) / fr.W, dy = (fr.hi[1] - fr.lo[1]) / fr.H;
+  const long ncubes = (long)N * N * N;
+#pragma omp parallel num_threads(T)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double* img = bufs + (size_t)tid * npix;
+#pragma omp for schedule(static)
+    for (long cube = 0; cube < ncubes; ++cube) {
+      long i = cube % N, j = (cube / N) % N, k = cube / ((long)N * N);
+      for (int s = 0; s < 6; ++s) {
+        double v[4][3];
+        tet_vertices(pos, N, box, i, j, k, s, v);
+        const double V = tet_volume(v);
+        if (V == 0.0) continue;
+        const double rho = m / fabs(V);
+        /* projected vertices in pixel units (pixel px covers [px, px + 1)) */
+        pt2 P[4];
+        for (int c = 0; c < 4; ++c) {
+          P[c].x = (dot3(fr.r, v[c]) - fr.lo[0]) / dx;
+          P[c].y = (dot3(fr.u, v[c]) - fr.lo[1]) / dy;
+        }
+        /* depth of each vertex along the view direction */
+        double z[4];
+        for (int c = 0; c < 4; ++c) z[c] = dot3(fr.f, v[c]);
+        /* the apex, the hull (counter-clockwise) and the chord at the apex:
+         * the depth of the back surface there minus that of the front one
+         * (Eq. 6). A vertex inside the triangle of the other three, or on its
+         * boundary (coincident projections, as for the undeformed lattice
+         * seen along an axis), is the apex; the chord there runs from it to
+         * the opposite face. */
+        pt2 apex, hull[4];
+        int nh = 0;
+        int inner = -1;
+        double chord = 0.0;
+        for (int c = 0; c < 4 && inner < 0; ++c) {
+          const int ia = (c + 1) & 3, ib = (c + 2) & 3, id = (c + 3) & 3;
+          const pt2 a = P[ia], b = P[ib], d = P[id];
+          const double o = orient2(a, b, d);
+          if (o == 0.0) continue;
+          /* barycentric coordinates of P[c] in triangle (a, b, d) */
+          const double la = orient2(b, d, P[c]) / o, lb = orient2(d, a, P[c]) / o, ld = orient2(a, b, P[c]) / o;
+          if (la >= 0.0 && lb >= 0.0 && ld >= 0.0) {
+            inner = c;
+            chord = fabs(z[c] - (la * z[ia] + lb * z[ib] + ld * z[id]));
+          }
+        }
+        if (inner >= 0) {
+          apex = P[inner];
+          for (int c = 0; c < 4; ++c)
+            if (c != inner) hull[nh++] = P[c];
+          if (orient2(hull[0], hull[1], hull[2]) < 0.0) { pt2 t = hull[1]; hull[1] = hull[2]; hull[2] = t; }
+        } else {
+          /* convex quadrilateral: find the order in which 0-a and b-c are the diagonals */
+          int a = -1;
+          for (int c = 1; c < 4 && a < 0; ++c) {
+            int o1 = c == 1 ? 2 : 1, o2 = 6 - c - o1;
+            const double s1 = orient2(P[0], P[c], P[o1]), s2 = orient2(P[0], P[c], P[o2]);
+            if ((s1 > 0.0 && s2 < 0.0) || (s1 < 0.0 && s2 > 0.0)) a = c;
+          }
+          if (a < 0) continue; /* no projected area */
+          const int b1 = a == 1 ? 2 : 1, b2 = 6 - a - b1;
+          /* diagonals P0-Pa and Pb1-Pb2 cross at the apex */
+          const double d1x = P[a].x - P[0].x, d1y = P[a].y - P[0].y;
+          const double d2x = P[b2].x - P[b1].x, d2y = P[b2].y - P[b1].y;
+          const double den = d1x * d2y - d1y * d2x;
+          if (den == 0.0) continue;
+          const double t = ((P[b1].x - P[0].x) * d2y - (P[b1].y - P[0].y) * d2x) / den;
+          const double u = ((P[b1].x - P[0].x) * d1y - (P[b1].y - P[0].y) * d1x) / den;
+          apex.x = P[0].x + t * d1x;
+          apex.y = P[0].y + t * d1y;
+          /* the chord at the crossing runs between the two diagonal edges */
+          chord = fabs((z[0] + t * (z[a] - z[0])) - (z[b1] + u * (z[b2] - z[b1])));
+          hull[0] = P[0]; hull[1] = P[b1]; hull[2] = P[a]; hull[3] = P[b2];
+          nh = 4;
+          if (orient2(hull[0], hull[1], hull[2]) < 0.0) { pt2 t2 = hull[1]; hull[1] = hull[3]; hull[3] = t2; }
+        }
+        const double h = rho * chord;
+        if (!(h > 0.0)) continue;
+        double xmn = P[0].x, xmx = P[0].x, ymn = P[0].y, ymx = P[0].y;
+        for (int c = 1; c < 4; ++c) {
+          xmn = fmin(xmn, P[c].x); xmx = fmax(xmx, P[c].x);
+          ymn = fmin(ymn, P[c].y); ymx = fmax(ymx, P[c].y);
+        }
+        const long x0 = (long)floor(xmn), x1 = (long)floor(xmx), y0 = (long)floor(ymn), y1 = (long)floor(ymx);
+        long sx0, sx1, sy0, sy1;
+        shift_range(x0, x1, 0, fr.W - 1, fr.W, fr.wrap, &sx0, &sx1);
+        shift_range(y0, y1, 0, fr.H - 1, fr.H, fr.wrap, &sy0, &sy1);
+        for (long sy = sy0; sy <= sy1; ++sy)
+          for (long sx = sx0; sx <= sx1; ++sx) {
+            const long px0 = x0 > -sx * fr.W ? x0 : -sx * fr.W, px1 = x1 < fr.W - 1 - sx * fr.W ? x1 : fr.W - 1 - sx * fr.W;
+            const long py0 = y0 > -sy * fr.H ? y0 : -sy * fr.H, py1 = y1 < fr.H - 1 - sy * fr.H ? y1 : fr.H - 1 - sy * fr.H;
+            for (long py = py0; py <= py1; ++py)
+              for (long px = px0; px <= px1; ++px) {
+                double sum = 0.0;
+                for (int e = 0; e < nh; ++e)
+                  sum += tri_square_integral(apex, hull[e], hull[(e + 1) % nh], h, (double)px, (double)px + 1.0,
+                                             (double)py, (double)py + 1.0);
+                img[(py + sy * fr.H) * fr.W + (px + sx * fr.W)] += sum;  /* area in pixels: the mean over the square */
+              }
+          }
+      }
+    }
+  }
+  memset(out, 0, sizeof(double) * npix);
+  for (int t = 0; t < T; ++t)
+    for (long p = 0; p < npix; ++p) out[p] += bufs[(size_t)t * npix + p];
+  free(bufs);
+  return ORC_OK;
 }

@@ -99,6 +99,8 @@ def _load():
         lib.orc_centroids.restype = C.c_int
         lib.orc_hybrid.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.POINTER(_Cam), C.c_double, dp, C.c_int]
         lib.orc_hybrid.restype = C.c_int
+        lib.orc_render_area.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.POINTER(_Cam), dp, C.c_int]
+        lib.orc_render_area.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -286,4 +288,18 @@ def hybrid(pos, N: int, cam, r_near: float, box: float = 1.0, total_mass: float 
                         nthreads)
     if rc != 0:
         raise RuntimeError(f"oracle hybrid failed with code {rc}")
+    return out
+
+
+def render_area(pos, N: int, cam, box: float = 1.0, total_mass: float = 1.0, nthreads: int = 0) -> np.ndarray:
+    """Area-averaged pixels of an orthographic view: each pixel holds the
+    mean of the column density (Eq. 6) over its square. Returns [H][W]."""
+    lib = _load()
+    cam = _cam(cam)
+    p = _pos64(pos, N)
+    out = np.zeros((cam.H, cam.W), dtype=np.float64)
+    cc = cam.to_c()
+    rc = lib.orc_render_area(_ptr(p, C.c_double), N, box, total_mass, C.byref(cc), _ptr(out, C.c_double), nthreads)
+    if rc != 0:
+        raise RuntimeError(f"oracle render_area failed with code {rc}")
     return out
