@@ -858,19 +858,25 @@ __device__ __forceinline__ void tet_f64(const Lattice& L, long long soff, int i,
   }
 }
 
-// Error model of a fragment's FP32 value (accumulator units), with e its
-// active pyramid edge (the smallest edge function):
-//   * the round-off of the edge function itself, relative, about kFragErr
-//     times the edge's steepness |e|^2 / min(|o1|, |o2|);
+// Error model of a fragment's FP32 value (accumulator units). Every hull edge
+// e gets a bound e_e on its FP32 edge function f_e:
 //   * the rounding of the projected vertex positions, absolute: the edge
-//     moves by up to delta pixels, changing the value by up to its slope
-//     (|a_e| + |b_e|) times delta. Thin projected slivers have huge slopes.
-// In perspective both are scaled by d value / d T = 1 / (M + g T)^2.
-// A fragment is recomputed exactly when the bound could exceed kFragTol of
-// max(value, mean column density); so is a pixel just outside the FP32 hull
-// that the vertex uncertainty could move inside.
+//     moves by up to delta pixels, changing f_e by up to its slope
+//     (|a_e| + |b_e|) times delta. Thin projected slivers have huge slopes;
+//   * the round-off of the edge's coefficients, relative, about kFragErr
+//     times the edge's steepness |e|^2 / min(|o1|, |o2|) times |f_e|;
+//   * the round-off of evaluating a X + b Y + c, absolute: kEvalErr times
+//     |a X| + |b Y| + |c|.
+// The pyramid is the minimum over the edges, and the edge that is smallest in
+// FP32 need not be the smallest in exact arithmetic: the true minimum lies in
+// [min (f_e - e_e), min (f_e + e_e)]. The FP32 value max(min f, 0) may be off
+// by its distance to the far end of that interval, scaled in perspective by
+// d value / d T = 1 / (M + g T)^2. A fragment is recomputed exactly when that
+// could exceed kFragTol of max(value, mean column density); a pixel just
+// outside the FP32 hull that the bounds could move inside is one of them.
 constexpr float kFragErr = 1e-5f;
 constexpr float kFragTol = 1e-5f;
+constexpr float kEvalErr = 4.0f / 16777216.0f;  // four ulp of the terms of a X + b Y + c
 
 // Vertex position uncertainty (pixels) of a tetrahedron whose vertices lie
 // within R pixels of its cube's anchor (R includes, in perspective, the
@@ -887,15 +893,32 @@ __device__ __forceinline__ float max_edge_slope(const TetRaster& t) {
                fmaxf(fabsf(t.a[2]) + fabsf(t.b[2]), fabsf(t.a[3]) + fabsf(t.b[3])));
 }
 
+// Largest evaluation round-off of the edge functions over the bounding box
+// (pixel coordinates up to R in magnitude).
+__device__ __forceinline__ float max_eval_error(const TetRaster& t, float R) {
+  float m = 0.0f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float ab = fabsf(t.a[e]) + fabsf(t.b[e]);
+    if (ab > 0.0f) m = fmaxf(m, kEvalErr * fmaf(ab, R, fabsf(t.c[e])));
+  }
+  return m;
+}
+
 // True when some fragment of a set-up tetrahedron may need the exact path:
-// with A the largest position term and B v the round-off term over values
-// v <= hmax, some v has A + B v > kFragTol max(v, sigma). Below sigma that
-// needs A + B min(hmax, sigma) > kFragTol sigma; above it, B >= kFragTol.
+// with A the largest position term, C the largest evaluation term and B v the
+// relative term over values v <= hmax (doubled: an edge within its bound of
+// the minimum can hold up to about twice the minimum's value), some v has
+// A + 2 B v + C > kFragTol max(v, sigma). Below sigma that needs
+// A + 2 B min(hmax, sigma) + C > kFragTol sigma; above it, 2 B >= kFragTol.
 __device__ __forceinline__ bool may_need_exact(const TetRaster& t, float sigma_units, float delta) {
   const float stmax = fmaxf(fmaxf(t.st[0], t.st[1]), fmaxf(t.st[2], t.st[3]));
+  const float R = fmaxf(fmaxf(fabsf(t.xmin), fabsf(t.xmax)), fmaxf(fabsf(t.ymin), fabsf(t.ymax)));
   const float A = max_edge_slope(t) * delta * t.vscale, B = stmax * kFragErr;
+  const float C = max_eval_error(t, R) * t.vscale;
   // written so that a non-finite coefficient (an extreme sliver) also flags
-  return !(A + B * fminf(t.hmax, sigma_units) <= kFragTol * sigma_units) || (t.hmax > sigma_units && B >= kFragTol);
+  return !(A + 2.0f * B * fminf(t.hmax, sigma_units) + C <= kFragTol * sigma_units) || !(B < 0.25f) ||
+         (t.hmax > sigma_units && 2.0f * B >= kFragTol);
 }
 
 // True when the vertex uncertainty could move a pixel whose value matters
@@ -905,19 +928,33 @@ __device__ __forceinline__ bool may_miss_fragments(const TetRaster& t, float sig
   return !(max_edge_slope(t) * delta * t.vscale <= kFragTol * sigma_units);
 }
 
+// Bound e_e of one edge function's FP32 value f at pixel (X, Y); 0 for an
+// unused slot (a = b = 0, a constant large c).
+__device__ __forceinline__ float edge_error(float f, float a, float b, float c, float st, float X, float Y,
+                                            float delta) {
+  const float ab = fabsf(a) + fabsf(b);
+  if (ab == 0.0f) return 0.0f;
+  return fmaf(ab, delta, fmaf(kFragErr * st, fabsf(f), kEvalErr * (fabsf(a * X) + fabsf(b * Y) + fabsf(c))));
+}
+
 // Exact-path decision for one candidate pixel of a flagged tetrahedron: f the
-// four edge functions there, a, b, st their gradients and steepness, dvdT
-// the perspective factor (1 orthographic), v the FP32 value.
+// four edge functions at pixel (X, Y), a, b, c, st their coefficients and
+// steepness, dvdT the perspective factor (1 orthographic), v the FP32 value.
 __device__ __forceinline__ bool fragment_needs_exact(float f0, float f1, float f2, float f3, float4 a, float4 b,
-                                                     float4 st, float delta, float dvdT, float v, float sigma_units) {
-  float mn = f0, ae = a.x, be = b.x, se = st.x;
-  if (f1 < mn) { mn = f1; ae = a.y; be = b.y; se = st.y; }
-  if (f2 < mn) { mn = f2; ae = a.z; be = b.z; se = st.z; }
-  if (f3 < mn) { mn = f3; ae = a.w; be = b.w; se = st.w; }
-  const float pos_err = (fabsf(ae) + fabsf(be)) * delta;
-  if (!(pos_err < 3.0e38f) || mn != mn) return true;  // non-finite edge function: evaluate exactly
-  if (!(mn > 0.0f)) return mn > -pos_err && pos_err * dvdT > kFragTol * sigma_units;
-  return (pos_err + kFragErr * se * mn) * dvdT > kFragTol * fmaxf(v, sigma_units);
+                                                     float4 c, float4 st, float X, float Y, float delta, float dvdT,
+                                                     float v, float sigma_units) {
+  const float e0 = edge_error(f0, a.x, b.x, c.x, st.x, X, Y, delta);
+  const float e1 = edge_error(f1, a.y, b.y, c.y, st.y, X, Y, delta);
+  const float e2 = edge_error(f2, a.z, b.z, c.z, st.z, X, Y, delta);
+  const float e3 = edge_error(f3, a.w, b.w, c.w, st.w, X, Y, delta);
+  if (f0 != f0 || f1 != f1 || f2 != f2 || f3 != f3) return true;  // non-finite edge function: evaluate exactly
+  const float lo = fminf(fminf(f0 - e0, f1 - e1), fminf(f2 - e2, f3 - e3));
+  const float hi = fminf(fminf(f0 + e0, f1 + e1), fminf(f2 + e2, f3 + e3));
+  if (!(hi > 0.0f) && hi == hi) return false;  // outside for certain
+  const float T = fmaxf(fminf(fminf(f0, f1), fminf(f2, f3)), 0.0f);
+  const float dev = fmaxf(T - fmaxf(lo, 0.0f), fmaxf(hi, 0.0f) - T);
+  // written so that a non-finite bound also takes the exact path
+  return !(dev * dvdT <= kFragTol * fmaxf(v, sigma_units));
 }
 
 // Number of periodic copies: shift range s in [s0, s1] such that the span

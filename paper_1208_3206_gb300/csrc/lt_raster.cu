@@ -86,8 +86,9 @@ __device__ __forceinline__ void cube_fragments(const CubeProj& P, const FrameDev
             }
             if (check && fragment_needs_exact(f0, f1, f2, f3, make_float4(t.a[0], t.a[1], t.a[2], t.a[3]),
                                               make_float4(t.b[0], t.b[1], t.b[2], t.b[3]),
-                                              make_float4(t.st[0], t.st[1], t.st[2], t.st[3]), delta, dvdT, v,
-                                              F.sigma_units)) {
+                                              make_float4(t.c[0], t.c[1], t.c[2], t.c[3]),
+                                              make_float4(t.st[0], t.st[1], t.st[2], t.st[3]), X, Y, delta, dvdT,
+                                              v, F.sigma_units)) {
               const double ex = exact_fragment(Lat, F, cube, s, sx, sy, px, py, F.m_tet);
               if (ex > 0.0) fn(px, py, (float)(ex / F.unit));
               continue;

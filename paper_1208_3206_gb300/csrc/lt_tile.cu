@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
                   // the exact evaluation
                   if (r6.w != 0.0f) {
                     const float q = persp ? __fdividef(M, den) : 1.0f;  // d value / d T = (M / den)^2
-                    exact = fragment_needs_exact(f0, f1, f2, f3, ra, rbv, R[7], R[8].w, q * q, v, sig);
+                    exact = fragment_needs_exact(f0, f1, f2, f3, ra, rbv, rc, R[7], fx, fy, R[8].w, q * q, v, sig);
                   }
                   if (!exact) {
                     if (v > 0.0f && LT_IN_BOUNDS(X >= 0 && X < tw && Y >= 0 && Y < th, &a.ctr->errors))
