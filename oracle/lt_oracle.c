@@ -253,9 +253,11 @@ static int num_threads(int req) {
  * (tetrahedron, pixel) pairs with a positive chord inside the crops, and
  * n_degen (optional) the number of tetrahedra with V == 0.
  */
-int orc_render(const double* pos, int N, double box, double total_mass, const orc_camera* cam,
-               const int* crops, int ncrops, double* out, long long* n_frag, long long* n_degen,
-               int nthreads) {
+/* The projection over the cubes listed in `sel` (nsel of them), or over
+ * every cube when sel is NULL. */
+static int render_cubes(const double* pos, int N, double box, double total_mass, const orc_camera* cam,
+                        const int* crops, int ncrops, const long long* sel, long nsel, double* out,
+                        long long* n_frag, long long* n_degen, int nthreads) {
   frame_t fr;
   if (N <= 0 || box <= 0 || ncrops <= 0 || frame_init(cam, &fr) != ORC_OK) return ORC_ERR_ARG;
   long total = 0;
@@ -269,7 +271,7 @@ int orc_render(const double* pos, int N, double box, double total_mass, const or
   long long* degen = (long long*)calloc(T, sizeof(long long));
   int* errs = (int*)calloc(T, sizeof(int));
   const double m = total_mass / (6.0 * (double)N * N * N);
-  const long ncubes = (long)N * N * N;
+  const long ncubes = sel ? nsel : (long)N * N * N;
 
 #pragma omp parallel num_threads(T)
   {
@@ -279,7 +281,9 @@ int orc_render(const double* pos, int N, double box, double total_mass, const or
 #endif
     double* img = bufs + (size_t)tid * total;
 #pragma omp for schedule(static)
-    for (long cube = 0; cube < ncubes; ++cube) {
+    for (long q = 0; q < ncubes; ++q) {
+      const long cube = sel ? (long)sel[q] : q;
+      if (cube < 0 || cube >= (long)N * N * N) { errs[tid] = ORC_ERR_ARG; continue; }
       long i = cube % N, j = (cube / N) % N, k = cube / ((long)N * N);
       for (int s = 0; s < 6; ++s) {
         double v[4][3];
@@ -335,6 +339,22 @@ int orc_render(const double* pos, int N, double box, double total_mass, const or
   if (n_degen) *n_degen = nd;
   free(bufs); free(frags); free(degen); free(errs); free(coff);
   return err;
+}
+
+int orc_render(const double* pos, int N, double box, double total_mass, const orc_camera* cam,
+               const int* crops, int ncrops, double* out, long long* n_frag, long long* n_degen,
+               int nthreads) {
+  return render_cubes(pos, N, box, total_mass, cam, crops, ncrops, NULL, 0, out, n_frag, n_degen, nthreads);
+}
+
+/* The same projection restricted to the listed cubes (ids i + N (j + N k)),
+ * for tests that need a few pixels of a large lattice: the caller picks every
+ * cube that can reach them. */
+int orc_render_subset(const double* pos, int N, double box, double total_mass, const orc_camera* cam,
+                      const int* crops, int ncrops, const long long* cubes, long ncubes, double* out,
+                      long long* n_frag, long long* n_degen, int nthreads) {
+  if (!cubes || ncubes < 0) return ORC_ERR_ARG;
+  return render_cubes(pos, N, box, total_mass, cam, crops, ncrops, cubes, ncubes, out, n_frag, n_degen, nthreads);
 }
 
 /* Per-tetrahedron signed volume (Eq. 9) and density (Eq. 3), tetrahedron

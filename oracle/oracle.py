@@ -99,6 +99,10 @@ def _load():
         lib.orc_centroids.restype = C.c_int
         lib.orc_hybrid.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.POINTER(_Cam), C.c_double, dp, C.c_int]
         lib.orc_hybrid.restype = C.c_int
+        lib.orc_render_subset.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.POINTER(_Cam), C.POINTER(C.c_int),
+                                          C.c_int, C.POINTER(C.c_longlong), C.c_long, dp,
+                                          C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.c_int]
+        lib.orc_render_subset.restype = C.c_int
         lib.orc_render_area.argtypes = [dp, C.c_int, C.c_double, C.c_double, C.POINTER(_Cam), dp, C.c_int]
         lib.orc_render_area.restype = C.c_int
         _lib = lib
@@ -120,9 +124,11 @@ def _cam(cam) -> Camera:
 
 
 def render_crops(pos, N: int, cam, crops: Sequence[Sequence[int]], box: float = 1.0,
-                 total_mass: float = 1.0, nthreads: int = 0):
+                 total_mass: float = 1.0, nthreads: int = 0, cubes=None):
     """Render the listed crops (x0, y0, w, h) of the frame; returns
-    (list of [h][w] float64 images, fragment count, degenerate count)."""
+    (list of [h][w] float64 images, fragment count, degenerate count).
+    `cubes`: optional cube ids (i + N (j + N k)) to draw instead of all of
+    them; the caller must list every cube that can reach the crops."""
     lib = _load()
     cam = _cam(cam)
     p = _pos64(pos, N)
@@ -131,8 +137,14 @@ def render_crops(pos, N: int, cam, crops: Sequence[Sequence[int]], box: float = 
     out = np.zeros(sum(sizes), dtype=np.float64)
     nf, nd = C.c_longlong(0), C.c_longlong(0)
     cc = cam.to_c()
-    rc = lib.orc_render(_ptr(p, C.c_double), N, box, total_mass, C.byref(cc), _ptr(cr, C.c_int),
-                        len(cr), _ptr(out, C.c_double), C.byref(nf), C.byref(nd), nthreads)
+    if cubes is None:
+        rc = lib.orc_render(_ptr(p, C.c_double), N, box, total_mass, C.byref(cc), _ptr(cr, C.c_int),
+                            len(cr), _ptr(out, C.c_double), C.byref(nf), C.byref(nd), nthreads)
+    else:
+        sel = np.ascontiguousarray(np.asarray(cubes, dtype=np.int64).ravel())
+        rc = lib.orc_render_subset(_ptr(p, C.c_double), N, box, total_mass, C.byref(cc), _ptr(cr, C.c_int),
+                                   len(cr), _ptr(sel, C.c_longlong), len(sel), _ptr(out, C.c_double),
+                                   C.byref(nf), C.byref(nd), nthreads)
     if rc != 0:
         raise RuntimeError(f"oracle render failed with code {rc}")
     imgs, o = [], 0

@@ -699,3 +699,28 @@ def test_supersampled_pixel_centres_converge_to_the_area_mean():
         errs.append(float(np.abs(s - area).max() / area.mean()))
     assert errs[2] <= 5e-3
     assert errs[2] < 0.5 * errs[1] < 0.5 * errs[0]
+
+
+def test_render_over_the_cubes_near_a_pixel_equals_the_full_render():
+    """The oracle's render restricted to the cubes that can reach some pixels
+    (the offset bound of tests/near_cubes.py) equals the full render there,
+    also for rays moved by a small fraction of a pixel; a subset that misses
+    the reaching cubes does not."""
+    from near_cubes import cubes_near_pixels
+    N, W = 32, 128
+    pos = ZeldovichField.generate(N, -2.0, 16.0, 321).positions(1.5)
+    cam = ortho_z(W, W)
+    full = oracle.render(pos, N, cam)
+    picks = [(5, 7), (70, 61), (127, 0)]
+    sel = cubes_near_pixels(pos, N, W, W, picks)
+    assert 0 < len(sel) < N ** 3
+    one = [(x, y, 1, 1) for x, y in picks]
+    got = [r[0, 0] for r in oracle.render_crops(pos, N, cam, one, cubes=sel)[0]]
+    np.testing.assert_array_equal(got, [full[y, x] for x, y in picks])
+    eps = 1e-4 / W
+    shifted = dict(cam, lo=(eps, -eps), hi=(1.0 + eps, 1.0 - eps))
+    a = [r[0, 0] for r in oracle.render_crops(pos, N, shifted, one, cubes=sel)[0]]
+    b = [r[0, 0] for r in oracle.render_crops(pos, N, shifted, one)[0]]
+    np.testing.assert_array_equal(a, b)
+    far = np.setdiff1d(np.arange(N ** 3), sel)
+    assert all(r[0, 0] == 0.0 for r in oracle.render_crops(pos, N, cam, one, cubes=far)[0])
