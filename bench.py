@@ -54,10 +54,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-atomic", action="store_true")
     ap.add_argument("--no-resample", action="store_true")
+    ap.add_argument("--no-area", action="store_true")
     ap.add_argument("--one-frame", action="store_true",
                     help="profiling case: bin frame 0 of the workload (snapshot 0, camera 0) and render it three "
                          "times with --tile; prints a summary instead of the JSON line")
     ap.add_argument("--tile", type=int, default=32)
+    ap.add_argument("--area-only", action="store_true",
+                    help="profiling case: the area-averaged pixel leg alone (128^3 lattice, orthographic 1024^2); "
+                         "prints its summary instead of the JSON line")
     ap.add_argument("--cpu-sample-crop", type=int, default=384)
     ap.add_argument("--oracle-crop", type=int, default=256, help="crop edge of the atomic form's oracle check")
     return ap.parse_args()
@@ -300,6 +304,10 @@ def run_lt(args, rank: int, world: int):
     resample = None if args.no_resample else bench_resample(dev)
     if resample is not None:
         log(f"resample: {resample['ms']:.1f} ms")
+    # area-averaged pixels of the 128^3 lattice, orthographic 1024^2
+    area = None if args.no_area else bench_area(dev)
+    if area is not None:
+        log(f"area-averaged pixels: {area['ms']:.2f} ms")
 
     # max over ranks
     if world > 1:
@@ -374,6 +382,8 @@ def run_lt(args, rank: int, world: int):
         line["atomic"] = atomic
     if resample is not None:
         line["resample"] = resample
+    if area is not None:
+        line["area"] = area
     # the GPU's pixels of frame 0's central crop (from the last end-to-end
     # step's host copy), for the parity figure next to the CPU baseline
     x0c, y0c, wc, hc = central_crop(cams[0], args.cpu_sample_crop)
@@ -440,6 +450,59 @@ def bench_resample(dev, n: int = 512, reps: int = 3):
                          "counted": f"{RESAMPLE_FLOPS_PER_INTERVAL} FP64 flops per interval + "
                                     f"{RESAMPLE_FLOPS_PER_PIECE} per slab piece",
                          "peak_from": "GB300 nominal FP64 rate"}}
+
+
+# FP32 operations lt_render_area counts per (tetrahedron, pixel) pair: the
+# eight lines (four hull edges, four rays) evaluated at the pixel's corner in
+# float-float (two error-free products, two two-sums and the small terms:
+# 20 operations, FMA as 2), and per pyramid face the corner tests (8); the
+# clip of partly covered squares is not counted.
+AREA_FLOPS_PER_PAIR = 8 * 20 + 4 * 8
+
+
+def bench_area(dev, reps: int = 5):
+    """Time lt_render_area (area-averaged pixels) of the 128^3 workload
+    (deformation eigenvalue 3) in the periodic orthographic 1024^2 view with
+    CUDA events; report frames/s, (tetrahedron, pixel) pairs per second and
+    the counted FP32 work against the FP32 peak."""
+    import torch
+
+    from lt_inputs import ZeldovichField, config, ortho_z
+    from paper_1208_3206_gb300.render import Renderer
+
+    c = config("zel128_ortho1024")
+    N, W, H = c["N"], c["W"], c["H"]
+    pos = torch.from_numpy(ZeldovichField.generate(N, c["n_index"], c["k_cut"], c["seed"]).positions(c["lams"][0]))
+    R = Renderer()
+    R.build_tets(pos.to(dev), N)
+    cam = ortho_z(W, H)
+    img = torch.empty((H, W), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        R.render_area(cam, image=img)
+    R.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        R.render_area(cam, image=img)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    st = R.get_stats()
+    mass = img.double().sum().item() / (W * H)
+    R.close()
+    pairs, p64 = st["area_pairs"], st["area_fp64_pairs"]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak, mhz, src = fp32_peak_tflops(sms)
+    achieved = AREA_FLOPS_PER_PAIR * pairs / (ms * 1e-3) / 1e12
+    return {"workload": f"zel128 lattice (12.6M tetrahedra), orthographic {W}x{H} periodic window",
+            "ms": ms, "value": 1e3 / ms, "unit": "frames/s", "pairs": pairs, "fp64_clip_pairs": p64,
+            "pairs_per_s": pairs / (ms * 1e-3), "frame_mass": mass,
+            "timing": "the whole call (frame upload, kernel, finalize, one host synchronisation)",
+            "roofline": {"bound": "alu", "kernel": "k_area (float-float lines + FP32 clip)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak,
+                         "counted": f"{AREA_FLOPS_PER_PAIR} FP32 flops per (tetrahedron, pixel) pair",
+                         "peak_from": f"{sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src})"}}
 
 
 def e2e_pipelined(pos, host_pos, img, host_img, N, cams, snaps, cfg, steps, barrier):
@@ -667,6 +730,10 @@ def main():
     args = parse()
     if args.one_frame:
         one_frame(args)
+        return
+    if args.area_only:
+        import torch
+        print(json.dumps(bench_area(torch.device("cuda", 0))), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

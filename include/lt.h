@@ -121,9 +121,13 @@ typedef struct {
   long long behind_eye;      /* cubes skipped because they straddle a perspective eye plane */
   long long range_overflow;  /* pixels that left the accumulator range */
   long long exact_fragments; /* ill-conditioned fragments re-evaluated in FP64 (cumulative) */
-  long long queue_overflow;  /* such fragments left in FP32 because a CTA's queue (32 per pixel of a tile) was full */
+  long long queue_overflow;  /* such fragments left in FP32 because a CTA's queue (64 per pixel of a tile) was full */
   long long resample_intervals; /* lt_resample: (tetrahedron, grid line) pairs of positive length, last call */
   long long resample_pieces;    /* lt_resample: their pieces in separate slabs (cell adds), last call */
+  long long area_pairs;         /* lt_render_area: (tetrahedron, pixel) pairs walked, last call */
+  long long area_fp64_pairs;    /* lt_render_area: of them, clipped in FP64 (hulls under 1/20 pixel wide) */
+  long long exact_tile_max;     /* most ill-conditioned fragments found in one tile since lt_create (the queue
+                                   holds 64 per pixel of a tile) */
   int n_frames;              /* frames of the last lt_project_bin */
   int tile;                  /* tile edge in use */
   int graph_kernels;         /* kernel nodes in the graph of the last lt_graph_build */
@@ -301,6 +305,29 @@ lt_status lt_slice(lt_ctx* ctx, int n, int weight, int snapshot, double z0, floa
  * fixed-point range latches LT_ERR_RANGE.
  */
 lt_status lt_render_centroids(lt_ctx* ctx, const lt_camera* cam, int snapshot, float* d_image, lt_stream stream);
+
+/*
+ * lt_render_area -- area-averaged pixels of one orthographic view (Sec. 3.2,
+ * Eq. 6 integrated over each pixel): pixel (x, y) holds the mean of the
+ * column density over its square (the window split into W x H equal
+ * squares) rather than its value at the pixel centre, so features thinner
+ * than a pixel keep their projected mass in the pixels they cross. Each
+ * tetrahedron's chord is integrated exactly: it is linear on the triangles
+ * joining the projected apex to the edges of the projected hull, and
+ * rho_t times the chord at the apex is 3 m / (hull area). A periodic window
+ * draws every periodic copy. Pixels are summed as 64-bit fixed-point integers
+ * (2^-frac_bits of the mean column density), so the image is bitwise
+ * reproducible and the frame mass is the projected mass up to that rounding.
+ * Tetrahedra with V == 0 carry nothing. lt_stats.area_pairs counts the
+ * (tetrahedron, pixel) pairs walked.
+ * d_image: float [H][W] (caller owned, overwritten). Synchronises; keeps an
+ * H x W array of 64-bit sums in the context; leaves the bins of
+ * lt_project_bin untouched.
+ * Errors: LT_ERR_STATE (no lt_build_tets), LT_ERR_ARG (null pointer, invalid
+ * or perspective camera, snapshot out of range), LT_ERR_NOMEM; a pixel
+ * leaving the fixed-point range latches LT_ERR_RANGE.
+ */
+lt_status lt_render_area(lt_ctx* ctx, const lt_camera* cam, int snapshot, float* d_image, lt_stream stream);
 
 /*
  * lt_render_hybrid -- hybrid near/far rendering of one perspective view

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblt.so")
 SOURCES = ["lt_api.cu", "lt_build.cu", "lt_bin.cu", "lt_tile.cu", "lt_raster.cu", "lt_backward.cu", "lt_static.cu",
-           "lt_resample.cu", "lt_slice.cu", "lt_centroids.cu"]
+           "lt_resample.cu", "lt_slice.cu", "lt_centroids.cu", "lt_area.cu"]
 HEADERS = ["lt_common.cuh", "lt_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

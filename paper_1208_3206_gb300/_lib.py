@@ -50,6 +50,9 @@ class LtStats(C.Structure):
         ("queue_overflow", C.c_longlong),
         ("resample_intervals", C.c_longlong),
         ("resample_pieces", C.c_longlong),
+        ("area_pairs", C.c_longlong),
+        ("area_fp64_pairs", C.c_longlong),
+        ("exact_tile_max", C.c_longlong),
         ("n_frames", C.c_int),
         ("tile", C.c_int),
         ("graph_kernels", C.c_int),
@@ -75,7 +78,7 @@ EXPORTS = [
     "lt_create", "lt_destroy", "lt_set_config", "lt_get_config", "lt_build_tets", "lt_project_bin",
     "lt_render_tiles", "lt_render_atomic", "lt_count_fragments", "lt_render_backward", "lt_graph_build",
     "lt_graph_launch", "lt_autotune", "lt_sync", "lt_get_stats", "lt_status_str", "lt_frame_mass_static",
-    "lt_resample", "lt_slice", "lt_render_centroids", "lt_render_hybrid",
+    "lt_resample", "lt_slice", "lt_render_centroids", "lt_render_area", "lt_render_hybrid",
 ]
 
 
@@ -142,6 +145,7 @@ def load(build_if_missing: bool = False):
         "lt_resample": ([vp, C.c_int, C.c_int, C.c_int, vp, vp], C.c_int),
         "lt_slice": ([vp, C.c_int, C.c_int, C.c_int, C.c_double, vp, vp], C.c_int),
         "lt_render_centroids": ([vp, cam_p, C.c_int, vp, vp], C.c_int),
+        "lt_render_area": ([vp, cam_p, C.c_int, vp, vp], C.c_int),
         "lt_render_hybrid": ([vp, cam_p, C.c_int, C.c_double, vp, vp], C.c_int),
     }
     for name, (args, res) in sigs.items():

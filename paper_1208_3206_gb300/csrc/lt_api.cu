@@ -752,6 +752,28 @@ lt_status lt_render_centroids(lt_ctx* ctx, const lt_camera* cam, int snapshot, f
   return centroids_impl(ctx, *cam, snapshot, d_image, false, (cudaStream_t)stream);
 }
 
+lt_status lt_render_area(lt_ctx* ctx, const lt_camera* cam, int snapshot, float* d_image, lt_stream stream) {
+  if (!ctx || !cam || !d_image) return LT_ERR_ARG;
+  if (!ctx->have_lattice) return LT_ERR_STATE;
+  if (snapshot < 0 || snapshot >= ctx->n_snap || cam->type != LT_ORTHO) return LT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  FrameDev F;
+  if (!make_frame(*cam, ctx, snapshot, ctx->cfg.tile, 0, F)) return LT_ERR_ARG;
+  lt_status st = grow(&ctx->d_frame_cen, &ctx->frame_cen_cap, 1);
+  if (st != LT_OK) return st;
+  const size_t np = (size_t)cam->W * cam->H;
+  if ((st = grow(&ctx->d_cacc, &ctx->cacc_cap, np)) != LT_OK) return st;
+  if ((st = grow_pinned(&ctx->h_frames, &ctx->h_frames_cap, 1)) != LT_OK) return st;
+  ctx->h_frames[0] = F;
+  LT_CUDA(cudaMemcpyAsync(ctx->d_frame_cen, ctx->h_frames, sizeof(FrameDev), cudaMemcpyHostToDevice, s));
+  LT_CUDA(cudaMemsetAsync(&ctx->d_ctr->area_pairs, 0, 2 * sizeof(unsigned long long), s));
+  // the fixed-point unit is the frame's: 2^-frac_bits of its mean column density
+  LT_CUDA(lt::launch_area(ctx->L, ctx->d_frame_cen, cam->W, cam->H, F.m_tet, F.unit, ctx->d_cacc, d_image, ctx->d_ctr,
+                          s));
+  LT_CUDA(cudaStreamSynchronize(s));
+  return LT_OK;
+}
+
 lt_status lt_render_hybrid(lt_ctx* ctx, const lt_camera* cam, int snapshot, double near_radius, float* d_image,
                            lt_stream stream) {
   if (!ctx || !cam || !d_image) return LT_ERR_ARG;
@@ -903,6 +925,9 @@ lt_status lt_get_stats(lt_ctx* ctx, lt_stats* out) {
   out->queue_overflow = (long long)c.queue_overflow;
   out->resample_intervals = (long long)c.resample_intervals;
   out->resample_pieces = (long long)c.resample_pieces;
+  out->area_pairs = (long long)c.area_pairs;
+  out->area_fp64_pairs = (long long)c.area_fp64_pairs;
+  out->exact_tile_max = (long long)c.exact_tile_max;
   out->n_frames = ctx->n_frames;
   out->tile = ctx->tile;
   out->graph_kernels = ctx->graph_kernels;

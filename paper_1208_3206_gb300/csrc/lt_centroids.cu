@@ -198,9 +198,14 @@ cudaError_t launch_centroids(const Lattice& L, const FrameDev* d_frame, int W, i
   k_centroids<<<(unsigned)(blocks < 1 ? 1 : blocks), 128, 0, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  return launch_fixed_finalize(d_acc, np, unit, add, d_out, s);
+}
+
+cudaError_t launch_fixed_finalize(const unsigned long long* d_acc, long long np, double unit, bool add, float* d_out,
+                                  cudaStream_t s) {
   long long fb = (np + 255) / 256;
   if (fb > 152LL * 32) fb = 152LL * 32;
-  k_centroids_finalize<<<(unsigned)fb, 256, 0, s>>>(d_acc, np, unit, add, d_out);
+  k_centroids_finalize<<<(unsigned)(fb < 1 ? 1 : fb), 256, 0, s>>>(d_acc, np, unit, add, d_out);
   return cudaGetLastError();
 }
 

@@ -72,6 +72,9 @@ struct DevCounters {
   unsigned long long queue_overflow;   // ill-conditioned fragments kept in FP32 (queue full)
   unsigned long long resample_intervals;  // (tetrahedron, grid line) pairs with a positive length
   unsigned long long resample_pieces;     // their pieces in separate slabs
+  unsigned long long area_pairs;          // lt_render_area: (tetrahedron, pixel) pairs walked
+  unsigned long long area_fp64_pairs;     // of them, clipped in FP64 (thin hulls)
+  unsigned long long exact_tile_max;      // most ill-conditioned fragments of one tile (queued or not)
 };
 
 // Snapshot description.

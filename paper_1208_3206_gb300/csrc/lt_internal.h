@@ -46,7 +46,7 @@ struct RasterArgs {
 cudaError_t launch_raster(const RasterArgs& a, int ctas, int threads, int any_persp, cudaStream_t s);
 int raster_max_ctas_per_sm(int threads, int tile, int any_persp);
 constexpr int kRasterMaxCtasPerSm = 4;     // CTAs per SM the exact queue is sized for
-constexpr unsigned kExactQueuePerPixel = 32;  // queued fragments per CTA and tile: 32 per pixel of the tile
+constexpr unsigned kExactQueuePerPixel = 64;  // queued fragments per CTA and tile: 64 per pixel of the tile
 cudaError_t launch_count_fragments(const RasterArgs& a, unsigned long long* d_counts, int n_frames, int ctas,
                                    int threads, cudaStream_t s);
 cudaError_t launch_mass_reduce(const double* mass_tile, long long tpf, int n_frames, double* d_mass,
@@ -72,6 +72,13 @@ cudaError_t launch_slice(const Lattice& L, int snapshot, int n, int weight, doub
 // the far cubes (cube_far) are drawn.
 cudaError_t launch_centroids(const Lattice& L, const FrameDev* d_frame, int W, int H, double m_tet, double unit,
                              unsigned long long* d_acc, float* d_out, bool add, DevCounters* ctr, cudaStream_t s);
+// 64-bit fixed-point sums (units of `unit`) to float, overwriting or adding to d_out.
+cudaError_t launch_fixed_finalize(const unsigned long long* d_acc, long long np, double unit, bool add, float* d_out,
+                                  cudaStream_t s);
+
+// ---- lt_area.cu: area-averaged pixels of one orthographic frame.
+cudaError_t launch_area(const Lattice& L, const FrameDev* d_frame, int W, int H, double m_tet, double unit,
+                        unsigned long long* d_acc, float* d_out, DevCounters* ctr, cudaStream_t s);
 
 // ---- lt_backward.cu
 cudaError_t launch_backward(const Lattice& L, const FrameDev* d_frames, long long stride, int n_frames, int n_snap,

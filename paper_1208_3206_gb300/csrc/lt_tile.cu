@@ -454,6 +454,7 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
     const unsigned nq = min(qn, a.xq_cap);
     if (threadIdx.x == 0 && qn) {
       atomicAdd(&a.ctr->exact_fragments, (unsigned long long)nq);
+      atomicMax(&a.ctr->exact_tile_max, (unsigned long long)qn);
       if (qn > a.xq_cap) atomicAdd(&a.ctr->queue_overflow, (unsigned long long)(qn - a.xq_cap));
     }
     for (unsigned qi = threadIdx.x; qi < nq; qi += blockDim.x) {

@@ -235,6 +235,19 @@ class Renderer:
         check("lt_render_centroids", self._lib.lt_render_centroids(self._h, arr, int(snapshot), _ptr(image), _stream()))
         return image
 
+    # -- lt_render_area
+    def render_area(self, cam, snapshot: int = 0, image: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Area-averaged pixels of one orthographic view: each pixel the mean
+        column density (Eq. 6) over its square. float32 [H][W]."""
+        cs, arr = _cams([cam])
+        c = cs[0]
+        if image is None:
+            image = torch.empty((c.H, c.W), dtype=torch.float32, device="cuda")
+        if image.dtype != torch.float32 or not image.is_cuda or image.numel() != c.H * c.W or not image.is_contiguous():
+            raise ValueError(f"image must be a contiguous float32 CUDA tensor with {c.H}x{c.W} elements")
+        check("lt_render_area", self._lib.lt_render_area(self._h, arr, int(snapshot), _ptr(image), _stream()))
+        return image
+
     # -- lt_render_hybrid
     def render_hybrid(self, cam, near_radius: float, snapshot: int = 0,
                       image: Optional[torch.Tensor] = None) -> torch.Tensor:
@@ -319,6 +332,10 @@ def lt_slice(r: Renderer, *a, **k):
 
 def lt_render_centroids(r: Renderer, *a, **k):
     return r.render_centroids(*a, **k)
+
+
+def lt_render_area(r: Renderer, *a, **k):
+    return r.render_area(*a, **k)
 
 
 def lt_render_hybrid(r: Renderer, *a, **k):

@@ -127,15 +127,20 @@ def test_fp16_512_workload_random_crops(R):
         e = np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)
         for iy, ix in zip(*np.nonzero(e > PIX_TOL)):
             bad.append((x + ix, y + iy, float(got[iy, ix]), float(ref[iy, ix])))
-    assert len(bad) <= 2e-3 * len(crops) * s * s
+    assert len(bad) <= 1e-4 * len(crops) * s * s
     if bad:
+        from near_cubes import cubes_near_pixels
         one = [(bx, by, 1, 1) for bx, by, _, _ in bad]
+        # only the cubes that can reach these pixels (the largest offset bounds
+        # how far a tetrahedron reaches from its cube)
+        B = float(np.abs(off[:, :3].astype(np.float32)).max())
+        sel = cubes_near_pixels(dec, N, W, H, [(bx, by) for bx, by, _, _ in bad], B=B)
         eps = 1e-4 / W
         limits = []
         for dx, dy in ((eps, 0.0), (-eps, 0.0), (0.0, eps), (0.0, -eps), (eps, eps), (eps, -eps), (-eps, eps),
                        (-eps, -eps)):
             shifted = dict(cam, lo=(dx, dy), hi=(1.0 + dx, 1.0 + dy))
-            limits.append([r[0, 0] for r in oracle.render_crops(dec, N, shifted, one)[0]])
+            limits.append([r[0, 0] for r in oracle.render_crops(dec, N, shifted, one, cubes=sel)[0]])
         limits = np.array(limits)
         for q, (bx, by, got, ref) in enumerate(bad):
             lo_v, hi_v = min(limits[:, q].min(), ref), max(limits[:, q].max(), ref)
