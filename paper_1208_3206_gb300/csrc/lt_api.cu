@@ -804,6 +804,9 @@ lt_status lt_graph_build(lt_ctx* ctx, const lt_camera* cams, int n_frames, const
     size_t cap = ctx->list_cap;
     if ((st = grow(&ctx->d_list, &cap, (size_t)want)) != LT_OK) return st;
     ctx->list_cap = cap;
+    // the reallocation dropped the lists just built: bin again, so that direct
+    // renders of these frames stay valid
+    if ((st = bin_launches(ctx, s, true)) != LT_OK) return st;
   }
   // the graph keeps its own copy of the frames, so that later direct calls
   // (which upload theirs into d_frames) leave its views unchanged

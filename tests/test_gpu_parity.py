@@ -217,6 +217,11 @@ def test_graph_replay_equals_direct_render(R):
         R.sync()
     torch.cuda.synchronize()
     assert torch.equal(img, direct)
+    # building the graph grows the bin list for headroom; the direct bins of
+    # the same frames must survive that
+    again = R.render_tiles()
+    R.sync()
+    assert torch.equal(again, direct)
 
 
 def test_error_paths(R):
