@@ -57,8 +57,9 @@ def parse():
     ap.add_argument("--no-area", action="store_true")
     ap.add_argument("--one-frame", action="store_true",
                     help="profiling case: bin frame 0 of the workload (snapshot 0, camera 0) and render it three "
-                         "times with --tile; prints a summary instead of the JSON line")
+                         "times with --tile and --raster-threads; prints a summary instead of the JSON line")
     ap.add_argument("--tile", type=int, default=32)
+    ap.add_argument("--raster-threads", type=int, default=256, help="raster CTA size of --one-frame")
     ap.add_argument("--area-only", action="store_true",
                     help="profiling case: the area-averaged pixel leg alone (128^3 lattice, orthographic 1024^2); "
                          "prints its summary instead of the JSON line")
@@ -359,6 +360,7 @@ def run_lt(args, rank: int, world: int):
             "unit": "TFLOP/s",
             "frac": achieved / peak,
             "traffic": raster_traffic(F),
+            "traffic_from": RASTER_TRAFFIC["capture"] if raster_traffic(F) is not None else None,
             "counted": f"{flops_per_frag} FP32 flops per fragment",
             "peak_from": f"{sms} SMs x 128 FP32 lanes x 2 x {peak_clock_mhz:.0f} MHz ({clock_src})",
             "raster_ms": raster_ms,
@@ -573,7 +575,10 @@ def e2e_pipelined(pos, host_pos, img, host_img, N, cams, snaps, cfg, steps, barr
 # DRAM bytes (read + write) of one k_tile launch per frame of the headline
 # workload, from an ncu capture of the kernel built from the sources whose
 # hash is recorded with it; None when the raster has changed since.
-RASTER_TRAFFIC = {"bytes_per_frame": None, "sources_sha16": None, "capture": None}
+RASTER_TRAFFIC = {"bytes_per_frame": 433693952, "sources_sha16": "3b41e56ca30bd8cd",
+                  "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_tile launch, "
+                             "python bench.py --one-frame --tile 64 --raster-threads 256 (frame 0), "
+                             "scaled by the frames"}
 
 
 def raster_sources_sha16() -> str:
@@ -701,7 +706,7 @@ def run_reference(args, rank: int, world: int):
 def one_frame(args):
     """A small case for profiler captures: the first frame of the workload
     (its snapshot alone on the device), binned once and rendered three
-    times with a fixed tile and 128-thread CTAs."""
+    times with a fixed tile and CTA size."""
     import torch
 
     from lt_inputs import ZeldovichField, config, ortho_z, sphere_cameras
@@ -714,7 +719,7 @@ def one_frame(args):
         cam = sphere_cameras(16, c["W"], c["H"], radius=c["radius"], fov_y_deg=c["fov_y_deg"])[0]
     else:
         cam = ortho_z(c["W"], c["H"])
-    R = Renderer(tile=args.tile, raster_threads=128)
+    R = Renderer(tile=args.tile, raster_threads=args.raster_threads)
     R.build_tets(torch.from_numpy(pos).cuda(), N)
     R.project_bin([cam])
     img = R.render_tiles()
@@ -722,7 +727,7 @@ def one_frame(args):
         R.render_tiles(image=img)
     R.sync()
     st = R.get_stats()
-    print(f"one frame of {args.workload}: tile {args.tile}, {st['entries']} bin entries, "
+    print(f"one frame of {args.workload}: tile {args.tile}, {args.raster_threads} threads, {st['entries']} bin entries, "
           f"{st['exact_fragments']} exact fragments over 3 renders, image sum {float(img.double().sum()):.6f}")
 
 

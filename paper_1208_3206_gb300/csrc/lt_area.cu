@@ -49,7 +49,7 @@ struct AreaArgs {
 struct AreaTet {
   float2 hull[4][3];  // hull edge e (from vertex e to e + 1): a x + b y + c >= 0 inside; (hi, lo) pairs
   float2 ray[4][3];   // ray from the apex through hull vertex e: >= 0 on the side of edge e
-  double k[4];        // column density per unit of hull line e
+  float k[4];         // column density per unit of hull line e, in accumulator units
   int n, ax, ay, thin;
   int x0, x1, y0, y1;
 };
@@ -88,9 +88,17 @@ __device__ __forceinline__ double line_f64(const float2* l, double ox, double oy
   return fma(join_ff(l[1]), oy, fma(join_ff(l[0]), ox, join_ff(l[2])));
 }
 
+// A thread's polygon buffer in shared memory: slot i of thread t at
+// p[i * kAreaThreads + t], so that the threads of a warp fall on distinct
+// banks whatever slots they touch.
+struct SmemPoly {
+  float* p;
+  __device__ __forceinline__ float& operator[](int i) const { return p[i * kAreaThreads]; }
+};
+
 // Clip the convex polygon (xi, yi)[n] to a x + b y + c >= 0 (Sutherland-Hodgman).
-template <typename T>
-__device__ __forceinline__ int clip_poly(const T* xi, const T* yi, int n, T a, T b, T c, T* xo, T* yo) {
+template <typename T, typename Buf>
+__device__ __forceinline__ int clip_poly(Buf xi, Buf yi, int n, T a, T b, T c, Buf xo, Buf yo) {
   int m = 0;
   T dp = c + a * xi[n - 1] + b * yi[n - 1];
   int j = n - 1;
@@ -114,9 +122,9 @@ __device__ __forceinline__ int clip_poly(const T* xi, const T* yi, int n, T a, T
 }
 
 // Integral over the unit square of the hull line function l0 = (a0, b0, c0),
-// restricted to l0 >= 0, l1 >= 0 and l2 >= 0.
-template <typename T>
-__device__ T sector_integral(T a0, T b0, T c0, T a1, T b1, T c1, T a2, T b2, T c2) {
+// restricted to l0 >= 0, l1 >= 0 and l2 >= 0; xa, ya, xb, yb hold 8 vertices each.
+template <typename T, typename Buf>
+__device__ T sector_integral(T a0, T b0, T c0, T a1, T b1, T c1, T a2, T b2, T c2, Buf xa, Buf ya, Buf xb, Buf yb) {
   const T la[3] = {a0, a1, a2}, lb[3] = {b0, b1, b2}, lc[3] = {c0, c1, c2};
   bool inside[3];
 #pragma unroll
@@ -128,8 +136,8 @@ __device__ T sector_integral(T a0, T b0, T c0, T a1, T b1, T c1, T a2, T b2, T c
     inside[l] = lo >= T(0);
   }
   if (inside[0] && inside[1] && inside[2]) return T(0.5) * (a0 + b0) + c0;
-  T xa[8] = {T(0), T(1), T(1), T(0)}, ya[8] = {T(0), T(0), T(1), T(1)};
-  T xb[8], yb[8];
+  xa[0] = T(0); xa[1] = T(1); xa[2] = T(1); xa[3] = T(0);
+  ya[0] = T(0); ya[1] = T(0); ya[2] = T(1); ya[3] = T(1);
   int n = 4;
   bool in_a = true;
 #pragma unroll
@@ -140,8 +148,8 @@ __device__ T sector_integral(T a0, T b0, T c0, T a1, T b1, T c1, T a2, T b2, T c
     in_a = !in_a;
     if (n < 3) return T(0);
   }
-  const T* x = in_a ? xa : xb;
-  const T* y = in_a ? ya : yb;
+  const Buf x = in_a ? xa : xb;
+  const Buf y = in_a ? ya : yb;
   // twice the area and six times the first moments, relative to vertex 0 (a
   // fan of triangles), so that a thin piece keeps its relative accuracy (the
   // square is counter-clockwise; clipping keeps it)
@@ -160,10 +168,10 @@ __device__ T sector_integral(T a0, T b0, T c0, T a1, T b1, T c1, T a2, T b2, T c
 }
 
 // Mean column density over pixel (ox, oy) (offsets from the anchor) of one
-// tetrahedron: the lines at the pixel's corner to about 2^-44 relative, the
-// clip in T.
-template <typename T>
-__device__ __forceinline__ double pixel_mean(const AreaTet& t, int ox, int oy) {
+// tetrahedron, in accumulator units: the lines at the pixel's corner to about
+// 2^-44 relative, the clip in T.
+template <typename T, typename Buf>
+__device__ __forceinline__ float pixel_mean(const AreaTet& t, int ox, int oy, Buf xa, Buf ya, Buf xb, Buf yb) {
   T ha[4], hb[4], hc[4], ra[4], rb[4], rc[4];
   // the hull lines first: a square outside one of them gets nothing
   bool outside = false;
@@ -194,13 +202,19 @@ __device__ __forceinline__ double pixel_mean(const AreaTet& t, int ox, int oy) {
       rc[e] = (T)line_f64(t.ray[e], (double)ox, (double)oy);
     }
   }
-  double v = 0.0;
+  T v = T(0);
   for (int e = 0; e < t.n; ++e) {
     const int f = e + 1 == t.n ? 0 : e + 1;
-    const T s = sector_integral<T>(ha[e], hb[e], hc[e], ra[e], rb[e], rc[e], -ra[f], -rb[f], -rc[f]);
-    v += t.k[e] * (double)s;
+    const T s = sector_integral<T, Buf>(ha[e], hb[e], hc[e], ra[e], rb[e], rc[e], -ra[f], -rb[f], -rc[f], xa, ya, xb, yb);
+    v += (T)t.k[e] * s;
   }
-  return v;
+  return (float)v;
+}
+
+// The FP64 clip of thin hulls, out of line (rare: it keeps the hot loop small).
+__device__ __noinline__ float pixel_mean_f64(const AreaTet& t, int ox, int oy) {
+  double xa[8], ya[8], xb[8], yb[8];
+  return pixel_mean<double, double*>(t, ox, oy, xa, ya, xb, yb);
 }
 
 // FP64 setup of the lane's tetrahedron; false when it covers no area.
@@ -300,13 +314,13 @@ __device__ bool setup_tet(const AreaArgs& a, const FrameDev& F, long long tau, A
     make_line(Hx[e] - t.ax, Hy[e] - t.ay, Hx[f] - Hx[e], Hy[f] - Hy[e], t.hull[e]);
     make_line(qx, qy, Hx[e] - Ax, Hy[e] - Ay, t.ray[e]);
     const double dA = join_ff(t.hull[e][0]) * qx + join_ff(t.hull[e][1]) * qy + join_ff(t.hull[e][2]);
-    t.k[e] = dA > 0.0 ? h / dA : 0.0;
+    t.k[e] = dA > 0.0 ? (float)(h / dA * a.inv_unit) : 0.0f;
     xmn = fmin(xmn, Hx[e]); xmx = fmax(xmx, Hx[e]);
     ymn = fmin(ymn, Hy[e]); ymx = fmax(ymx, Hy[e]);
   }
   for (int e = n; e < 4; ++e) {
     for (int q = 0; q < 3; ++q) t.hull[e][q] = t.ray[e][q] = make_float2(0.f, 0.f);
-    t.k[e] = 0.0;
+    t.k[e] = 0.0f;
   }
   t.n = n;
   t.thin = 0.5 * area2 < kThinHull * emax;
@@ -326,6 +340,9 @@ __device__ bool setup_tet(const AreaArgs& a, const FrameDev& F, long long tau, A
 
 __global__ void __launch_bounds__(kAreaThreads) k_area(AreaArgs a) {
   __shared__ AreaTet tets[kAreaThreads];
+  __shared__ float poly[4 * 8 * kAreaThreads];  // the FP32 clip's vertex buffers
+  const SmemPoly pxa{poly + threadIdx.x}, pya{poly + 8 * kAreaThreads + threadIdx.x};
+  const SmemPoly pxb{poly + 16 * kAreaThreads + threadIdx.x}, pyb{poly + 24 * kAreaThreads + threadIdx.x};
   const FrameDev& F = *a.frame;
   const int W = F.W, H = F.H;
   const long long ntet = 6LL * a.L.n_particles;
@@ -352,10 +369,10 @@ __global__ void __launch_bounds__(kAreaThreads) k_area(AreaArgs a) {
         const int ry = p / wx;
         const int px = t.x0 + (p - ry * wx), py = t.y0 + ry;
         const int ox = px - t.ax, oy = py - t.ay;
-        const double v = t.thin ? pixel_mean<double>(t, ox, oy) : pixel_mean<float>(t, ox, oy);
+        const float v = t.thin ? pixel_mean_f64(t, ox, oy) : pixel_mean<float, SmemPoly>(t, ox, oy, pxa, pya, pxb, pyb);
         const int pxw = F.wrap ? ((px % W) + W) % W : px, pyw = F.wrap ? ((py % H) + H) % H : py;
         if (!LT_IN_BOUNDS(pxw >= 0 && pxw < W && pyw >= 0 && pyw < H, &a.ctr->errors)) continue;
-        accum_fixed(a.acc + ((long long)pyw * W + pxw), (float)(v * a.inv_unit), a.ctr);
+        accum_fixed(a.acc + ((long long)pyw * W + pxw), v, a.ctr);
       }
     }
     __syncwarp();
