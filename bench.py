@@ -206,6 +206,7 @@ def run_lt(args, rank: int, world: int):
         for _ in range(args.warmup):
             R.graph_launch(stream)
     stream.synchronize()
+    exact_before = R.get_stats()["exact_fragments"]
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
@@ -224,6 +225,8 @@ def run_lt(args, rank: int, world: int):
     clk = clocks.stop()
     log(f"timed: {ms:.1f} ms per step")
     R.sync()
+    tstats = R.get_stats()
+    exact_per_step = (tstats["exact_fragments"] - exact_before) / args.steps
 
     # raster kernel alone (the dominant kernel), timed with events on its
     # stream; the project-and-bin pass before it is timed too (it includes one
@@ -369,6 +372,9 @@ def run_lt(args, rank: int, world: int):
             "build_ms": build_ms,
             "build": "lt_build_tets of all snapshots, once per set of positions (outside the step)",
             "bin_ms_per_step": bin_ms,
+            "exact_fragments_per_step": exact_per_step,
+            "exact_fragments": "fragments the per-fragment error test sent to the FP64 path, mean over the "
+                               "timed steps",
             "raster_ms_per_step": raster_ms,
             "step_ms": ms,
         },

@@ -125,7 +125,8 @@ typedef struct {
   long long resample_intervals; /* lt_resample: (tetrahedron, grid line) pairs of positive length, last call */
   long long resample_pieces;    /* lt_resample: their pieces in separate slabs (cell adds), last call */
   long long area_pairs;         /* lt_render_area: (tetrahedron, pixel) pairs walked, last call */
-  long long area_fp64_pairs;    /* lt_render_area: of them, clipped in FP64 (hulls under 1/20 pixel wide) */
+  long long area_fp64_pairs;    /* lt_render_area: of them, clipped in FP64 (hulls under 1/20 pixel wide, or an
+                                   apex within 1e-3 pixel of a hull edge) */
   long long exact_tile_max;     /* most ill-conditioned fragments found in one tile since lt_create (the queue
                                    holds 64 per pixel of a tile) */
   int n_frames;              /* frames of the last lt_project_bin */

@@ -24,8 +24,9 @@
 // GB300's FP64 pipe is narrow), so a line's offset there carries only its own
 // rounding, however far the pixel lies from the apex. The lane clips the
 // square against each triangle and sums the integrals. That step runs in FP32,
-// or in FP64 for hulls thinner than kThinHull pixels: there FP32 rounding of
-// the clip would show next to the pixel's own small value. The sums are 64-bit
+// or in FP64 for hulls thinner than kThinHull pixels and for apexes within
+// kThinSector pixels of a hull edge: there FP32 rounding of the clip would
+// show next to the pixel's own small value. The sums are 64-bit
 // fixed-point integers added by global atomics, so the image is bitwise
 // reproducible. A second kernel converts them to float.
 #include "lt_internal.h"
@@ -34,7 +35,8 @@ namespace lt {
 
 namespace {
 
-constexpr double kThinHull = 0.05;  // pixels: hull width below which the clip runs in FP64
+constexpr double kThinHull = 0.05;     // pixels: hull width below which the clip runs in FP64
+constexpr double kThinSector = 1e-3;  // pixels: apex distance to a hull edge below which it does too
 constexpr int kAreaThreads = 128;
 
 struct AreaArgs {
@@ -309,12 +311,16 @@ __device__ bool setup_tet(const AreaArgs& a, const FrameDev& F, long long tau, A
   t.ay = (int)fmin(fmax(floor(Ay), -1.0e9), 1.0e9);
   const double qx = Ax - t.ax, qy = Ay - t.ay;
   double xmn = Hx[0], xmx = Hx[0], ymn = Hy[0], ymx = Hy[0];
+  bool thin_sector = false;
   for (int e = 0; e < n; ++e) {
     const int f = e + 1 == n ? 0 : e + 1;
     make_line(Hx[e] - t.ax, Hy[e] - t.ay, Hx[f] - Hx[e], Hy[f] - Hy[e], t.hull[e]);
     make_line(qx, qy, Hx[e] - Ax, Hy[e] - Ay, t.ray[e]);
     const double dA = join_ff(t.hull[e][0]) * qx + join_ff(t.hull[e][1]) * qy + join_ff(t.hull[e][2]);
     t.k[e] = dA > 0.0 ? (float)(h / dA * a.inv_unit) : 0.0f;
+    // an apex next to a hull edge: a long thin face whose FP32 clip would lose
+    // its relative accuracy while k_e grows as 1 / dA
+    thin_sector = thin_sector || (dA > 0.0 && dA < kThinSector);
     xmn = fmin(xmn, Hx[e]); xmx = fmax(xmx, Hx[e]);
     ymn = fmin(ymn, Hy[e]); ymx = fmax(ymx, Hy[e]);
   }
@@ -323,7 +329,7 @@ __device__ bool setup_tet(const AreaArgs& a, const FrameDev& F, long long tau, A
     t.k[e] = 0.0f;
   }
   t.n = n;
-  t.thin = 0.5 * area2 < kThinHull * emax;
+  t.thin = 0.5 * area2 < kThinHull * emax || thin_sector;
   int x0 = (int)fmax(floor(xmn), -2.0e9), x1 = (int)fmin(floor(xmx), 2.0e9);
   int y0 = (int)fmax(floor(ymn), -2.0e9), y1 = (int)fmin(floor(ymx), 2.0e9);
   if (!F.wrap) {

@@ -281,10 +281,15 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
             qy0 = max(0, (int)ceilf(by0 - oy - margin));
             const int qy1 = min(th - 1, (int)floorf(by1 - oy + margin));
             if (qx0 <= qx1 && qy0 <= qy1) {
+              // the raster form relative to the bounding box's first pixel:
+              // small coordinates keep the round-off of evaluating a x + b y + c
+              // (and with it the exact path's share) small
+              const float lx = (float)qx0, ly = (float)qy0;
               const bool set =
-                  persp ? tet_setup<true>(x0, y0, x1, y1, x2, y2, x3, y3, pdw[0], pdw[1], pdw[2], pdw[3], Kn, ci.x,
-                                          invKn, t)
-                        : tet_setup<false>(x0, y0, x1, y1, x2, y2, x3, y3, 0.f, 0.f, 0.f, 0.f, Kn, 0.f, 0.f, t);
+                  persp ? tet_setup<true>(x0 - lx, y0 - ly, x1 - lx, y1 - ly, x2 - lx, y2 - ly, x3 - lx, y3 - ly,
+                                          pdw[0], pdw[1], pdw[2], pdw[3], Kn, ci.x, invKn, t)
+                        : tet_setup<false>(x0 - lx, y0 - ly, x1 - lx, y1 - ly, x2 - lx, y2 - ly, x3 - lx, y3 - ly,
+                                           0.f, 0.f, 0.f, 0.f, Kn, 0.f, 0.f, t);
               if (set) nrows = qy1 - qy0 + 1;
             }
           }
@@ -326,37 +331,40 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
             const int o = rprev + __popc(rmask & le_mask) - 1;
             rprev += __popc(rmask);
             // ---- 3. pixel span of each job's row: every edge function >= 0
-            int len = 0, xa = 0, Yr = 0;
+            // (coordinates relative to the record's bounding-box corner)
+            int len = 0, xl = 0, yl = 0, abase = 0;
             if (rb + lane < rtotal) {
               const float4* R = reinterpret_cast<const float4*>(recs + o * kRec);
               const float4 r0 = R[0];
-              Yr = __float_as_int(r0.y) + (rb + lane - __float_as_int(r0.w));
-              const float fy = (float)Yr;
+              yl = rb + lane - __float_as_int(r0.w);
+              const float fy = (float)yl;
               const float4 ra = R[1], rbv = R[2], rc = R[3], ri = R[4];
               float lo = __int_as_float(0xff800000), hi = __int_as_float(0x7f800000);
               span_edge(ra.x, fmaf(rbv.x, fy, rc.x), ri.x, lo, hi);
               span_edge(ra.y, fmaf(rbv.y, fy, rc.y), ri.y, lo, hi);
               span_edge(ra.z, fmaf(rbv.z, fy, rc.z), ri.z, lo, hi);
               span_edge(ra.w, fmaf(rbv.w, fy, rc.w), ri.w, lo, hi);
-              const int qx1w = __float_as_int(r0.z);
-              const float qx0f = (float)__float_as_int(r0.x), qx1f = (float)(qx1w & 0xffff);
+              const int qx0 = __float_as_int(r0.x), qy0 = __float_as_int(r0.y), qx1w = __float_as_int(r0.z);
+              const float wf = (float)((qx1w & 0xffff) - qx0);  // last pixel of the box, local
               if (qx1w >> 16) {
                 // a steep sliver: the whole bounding-box row, so that pixels the
                 // vertex uncertainty could move inside are checked too
-                lo = qx0f;
-                hi = qx1f;
+                lo = 0.0f;
+                hi = wf;
               }
-              lo = fmaxf(lo - 1e-3f, qx0f);
-              hi = fminf(hi + 1e-3f, qx1f);
+              lo = fmaxf(lo - 1e-3f, 0.0f);
+              hi = fminf(hi + 1e-3f, wf);
               if (lo <= hi) {
-                xa = (int)ceilf(lo);
-                len = max(0, (int)floorf(hi) - xa + 1);
+                xl = (int)ceilf(lo);
+                len = max(0, (int)floorf(hi) - xl + 1);
               }
+              abase = (qy0 + yl) * AS + qx0 + xl;  // accumulator index of the span's first pixel
             }
             int ptotal;
             const int poff = warp_excl_scan(len, ptotal);
             const int jslot = __popc(__ballot_sync(FULL, len > 0) & lt_mask);
-            if (len > 0 && LT_IN_BOUNDS(jslot < 32 && o < 32, &a.ctr->errors)) jobs[jslot] = make_int4(xa, Yr, o, poff);
+            if (len > 0 && LT_IN_BOUNDS(jslot < 32 && o < 32, &a.ctr->errors))
+              jobs[jslot] = make_int4(xl | (yl << 16), abase, o, poff);
             __syncwarp();
             // ---- 4. walk the pixels of the jobs, 32 per step
             int pprev = 0;
@@ -368,12 +376,13 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
               bool exact = false;
               unsigned long long qent = 0;
               float vq = 0.f;
-              int Xq = 0, Yq = 0;
+              int aq = 0;
               if (pb + lane < ptotal) {
                 const int4 J = jobs[j];
-                const int X = J.x + (pb + lane - J.w), Y = J.y;
+                const int kx = pb + lane - J.w;  // position within the job's span
+                const int ai = J.y + kx;         // accumulator index
                 const float4* R = reinterpret_cast<const float4*>(recs + J.z * kRec);
-                const float fx = (float)X, fy = (float)Y;
+                const float fx = (float)((J.x & 0xffff) + kx), fy = (float)(J.x >> 16);
                 const float4 ra = R[1], rbv = R[2], rc = R[3];
                 const float f0 = fmaf(ra.x, fx, fmaf(rbv.x, fy, rc.x));
                 const float f1 = fmaf(ra.y, fx, fmaf(rbv.y, fy, rc.y));
@@ -403,15 +412,15 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
                     exact = fragment_needs_exact(f0, f1, f2, f3, ra, rbv, rc, R[7], fx, fy, R[8].w, q * q, v, sig);
                   }
                   if (!exact) {
-                    if (v > 0.0f && LT_IN_BOUNDS(X >= 0 && X < tw && Y >= 0 && Y < th, &a.ctr->errors))
-                      accum_fixed(&acc[Y * AS + X], v, a.ctr);
+                    if (v > 0.0f && LT_IN_BOUNDS(ai >= 0 && ai % AS < tw && ai / AS < th, &a.ctr->errors))
+                      accum_fixed(&acc[ai], v, a.ctr);
                   } else {
                     const float4 r8 = R[8];
+                    const int Y = ai / AS, X = ai - Y * AS;  // tile pixel of the queued fragment
                     qent = pack_frag((unsigned)__float_as_int(r8.z), __float_as_int(r8.x), __float_as_int(r8.y),
                                      X, Y);
                     vq = v;
-                    Xq = X;
-                    Yq = Y;
+                    aq = ai;
                   }
                 }
               }
@@ -428,7 +437,7 @@ __global__ void __launch_bounds__(256, LT_TILE_MIN_CTAS) k_tile(RasterArgs a, un
                       xq[slot] = qent;
                     } else if (vq > 0.0f) {
                       // queue full: keep the FP32 value (counted in the statistics)
-                      accum_fixed(&acc[Yq * AS + Xq], vq, a.ctr);
+                      accum_fixed(&acc[aq], vq, a.ctr);
                     }
                   }
                 }
