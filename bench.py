@@ -581,7 +581,7 @@ def e2e_pipelined(pos, host_pos, img, host_img, N, cams, snaps, cfg, steps, barr
 # DRAM bytes (read + write) of one k_tile launch per frame of the headline
 # workload, from an ncu capture of the kernel built from the sources whose
 # hash is recorded with it; None when the raster has changed since.
-RASTER_TRAFFIC = {"bytes_per_frame": 433693952, "sources_sha16": "3b41e56ca30bd8cd",
+RASTER_TRAFFIC = {"bytes_per_frame": 432438784, "sources_sha16": "d73758b9859dd0d8",
                   "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_tile launch, "
                              "python bench.py --one-frame --tile 64 --raster-threads 256 (frame 0), "
                              "scaled by the frames"}
