@@ -47,3 +47,17 @@ def test_fp32_peak_from_unit_counts_and_clock():
     peak, mhz, src = bench.fp32_peak_tflops(152)
     assert mhz > 0 and src
     assert abs(peak - 152 * 128 * 2 * mhz * 1e-6) < 1e-9
+
+
+def test_raster_traffic_follows_the_captured_sources(monkeypatch):
+    """The raster's DRAM traffic in the bench line is the per-frame capture
+    scaled by the frames, and only while the raster's sources hash to the
+    captured ones: after any change to them it reads as unmeasured."""
+    cap = dict(bench.RASTER_TRAFFIC)
+    monkeypatch.setattr(bench, "RASTER_TRAFFIC", dict(cap, sources_sha16=bench.raster_sources_sha16()))
+    assert bench.raster_traffic(128) == cap["bytes_per_frame"] * 128
+    monkeypatch.setattr(bench, "RASTER_TRAFFIC", dict(cap, sources_sha16="0" * 16))
+    assert bench.raster_traffic(128) is None
+    monkeypatch.setattr(bench, "RASTER_TRAFFIC", dict(cap, bytes_per_frame=None))
+    assert bench.raster_traffic(128) is None
+
