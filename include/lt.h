@@ -303,7 +303,8 @@ lt_status lt_slice(lt_ctx* ctx, int n, int weight, int snapshot, double z0, floa
  * 64-bit sums in the context; leaves the bins of lt_project_bin untouched.
  * Errors: LT_ERR_STATE (no lt_build_tets), LT_ERR_ARG (null pointer,
  * invalid camera, snapshot out of range), LT_ERR_NOMEM; a pixel leaving the
- * fixed-point range latches LT_ERR_RANGE.
+ * fixed-point range, or a splat covering more than 2^31 pixels of the window
+ * (which is then left out), latches LT_ERR_RANGE.
  */
 lt_status lt_render_centroids(lt_ctx* ctx, const lt_camera* cam, int snapshot, float* d_image, lt_stream stream);
 
@@ -326,7 +327,8 @@ lt_status lt_render_centroids(lt_ctx* ctx, const lt_camera* cam, int snapshot, f
  * lt_project_bin untouched.
  * Errors: LT_ERR_STATE (no lt_build_tets), LT_ERR_ARG (null pointer, invalid
  * or perspective camera, snapshot out of range), LT_ERR_NOMEM; a pixel
- * leaving the fixed-point range latches LT_ERR_RANGE.
+ * leaving the fixed-point range, or a tetrahedron covering more than 2^31
+ * pixels of the window (which is then left out), latches LT_ERR_RANGE.
  */
 lt_status lt_render_area(lt_ctx* ctx, const lt_camera* cam, int snapshot, float* d_image, lt_stream stream);
 

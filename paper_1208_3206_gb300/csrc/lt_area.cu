@@ -341,7 +341,14 @@ __device__ bool setup_tet(const AreaArgs& a, const FrameDev& F, long long tau, A
     y1 = min(y1, y0 + 4 * F.H);
   }
   t.x0 = x0; t.x1 = x1; t.y0 = y0; t.y1 = y1;
-  return x0 <= x1 && y0 <= y1;
+  if (x0 > x1 || y0 > y1) return false;
+  if ((long long)(x1 - x0 + 1) * (y1 - y0 + 1) > 0x7fffffffLL) {
+    // more than 2^31 pixels (a window zoomed far into one tetrahedron): the
+    // walk's 32-bit pixel index cannot hold it
+    atomicOr(&a.ctr->errors, kErrRange);
+    return false;
+  }
+  return true;
 }
 
 __global__ void __launch_bounds__(kAreaThreads) k_area(AreaArgs a) {

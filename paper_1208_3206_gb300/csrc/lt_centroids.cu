@@ -112,6 +112,12 @@ __global__ void __launch_bounds__(128) k_centroids(CentroidArgs a) {
           syh = (float)(ph / h);
           norm = (float)(a.m_tet * 10.0 / (7.0 * M_PI * h * h) * a.inv_unit);
           live = front && x0 <= x1 && y0 <= y1;
+          if (live && (long long)(x1 - x0 + 1) * (y1 - y0 + 1) > 0x7fffffffLL) {
+            // more than 2^31 pixels (a window zoomed far into one splat): the
+            // walk's 32-bit pixel index cannot hold it
+            atomicOr(&a.ctr->errors, kErrRange);
+            live = false;
+          }
         }
       }
     }
